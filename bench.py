@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 BatchLayout path.
+
+Headline workload: exact-mode BatchLayout (Algorithm 2) on a Barabasi-Albert
+graph, n = 65,536, m = 4 (262,134 undirected edges), FP32 positions uniform in
+[-1,1)^2 from seed 0, minibatch 256. One step = one layout iteration (all 256
+minibatches: repulsion over all n, CSR attraction, update, step schedule),
+launched on its own, with L2 flushed between steps outside the timed events.
+Metric: pair-interactions/s = n(n-1) per iteration / device time.
+
+Secondary lines (in "also"): Barnes-Hut on R-MAT scale 20 (vertex-updates/s)
+and the batched small-graph launch, when those paths are built.
+
+--impl reference runs the FP64 CPU oracle on the host cores on a bounded sample
+of the same workload (the paper's method has no other runnable implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s & vertex-updates/s per iter; served layouts/s, p50/p99"
+SMS = 152
+MUFU_PER_CLK_PER_SM = 16      # rcp.approx.f32 lanes per clock per SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-also", action="store_true", help="headline workload only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# headline: exact mode, BA n=65,536, minibatch 256
+# ---------------------------------------------------------------------------
+
+BATCH = 256
+
+
+def exact_graph():
+    from paper_2002_08233_gb300 import synth
+    return synth.ba_65536()
+
+
+def run_exact(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2002_08233_gb300 import core, synth
+
+    torch.cuda.set_device(local)
+    core.load()
+    stream = core.use_torch()
+    g = exact_graph()
+    n = g.n
+    pairs_per_iter = float(n) * float(n - 1)
+    G = core.Graph(g)
+    x0 = synth.uniform_positions(n, 0)
+    L = core.Layout(G, xy=x0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    for _ in range(max(args.warmup, 0)):
+        L.run(1, BATCH, "exact")
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        L.run(1, BATCH, "exact")
+        ends[k].record(stream)
+        kernel_ms.append(L.stats()["last_run_ms"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = pairs_per_iter * args.steps * world / (total_ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    host_in = torch.from_numpy(x0.copy()).pin_memory()
+    host_out = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    hin = host_in.numpy()
+    hout = host_out.numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    L2 = core.Layout(G, xy=x0)
+    L2.run(1, BATCH, "exact")
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        L2.set_positions(hin, start_iter=k)
+        L2.run(1, BATCH, "exact")
+        L2.positions(out=hout)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = pairs_per_iter * e2e_steps * world / e2e_s
+
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_pairs = SMS * MUFU_PER_CLK_PER_SM * sm_max * 1e6
+    avg_kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = pairs_per_iter / avg_kernel_s
+    energy = float(L.stats()["energy"])
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "pair-interactions/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": "exact BatchLayout, Barabasi-Albert n=65,536 m=4 (262,134 edges), "
+                        "minibatch 256, one iteration per step",
+            "n": n, "nnz": g.nnz, "batch": BATCH, "mode": "exact",
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between steps (256 MB write outside the timed events)",
+            "init": "SplitMix64 seed 0, uniform [-1,1)^2",
+        },
+        "vertex_updates_per_s": n * args.steps * world / (total_ms / 1e3),
+        "kernel_ms_mean": statistics.mean(kernel_ms),
+        "wall_s": wall,
+        "energy_last": energy,
+        "e2e": {"value": e2e_value, "unit": "pair-interactions/s",
+                "h2d_bytes_per_step": int(host_in.numel() * 4),
+                "d2h_bytes_per_step": int(host_out.numel() * 4),
+                "steps": e2e_steps},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9,
+                     "unit": "G pair-interactions/s (1 SFU reciprocal per pair)",
+                     "frac": achieved / peak_pairs, "traffic": None,
+                     "kernel": "exact_grid_kernel",
+                     "peak_source": f"{SMS} SMs x {MUFU_PER_CLK_PER_SM} SFU lanes/clk x "
+                                    f"{sm_max:.0f} MHz ({src} sm_max_mhz)"},
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+    }
+    return out, g
+
+
+def _oracle_batches(g, x0, nb, cores):
+    """The oracle's forces for the first nb minibatches of iteration 0, each
+    followed by Algorithm 2's update, in order."""
+    import numpy as np
+
+    import oracle
+    xy = x0.astype(np.float64)
+    for b in range(nb):
+        lo, hi = b * BATCH, min(g.n, (b + 1) * BATCH)
+        f, _ = oracle.forces(g, xy, lo=lo, hi=hi, nthreads=cores)
+        nf = np.linalg.norm(f, axis=1)
+        mv = nf > 0
+        xy[lo:hi][mv] += f[mv] / nf[mv, None]
+    return xy
+
+
+def cpu_baseline_exact(g, seconds_target=15.0):
+    """The FP64 oracle on all host cores, on a bounded sample: whole minibatches
+    of the same workload, timed."""
+    from paper_2002_08233_gb300 import synth
+    cores = os.cpu_count() or 1
+    x0 = synth.uniform_positions(g.n, 0)
+    t0 = time.perf_counter()
+    _oracle_batches(g, x0, 1, cores)
+    probe = time.perf_counter() - t0
+    nb = int(max(1, min(g.n // BATCH, seconds_target / max(probe, 1e-3))))
+    t0 = time.perf_counter()
+    _oracle_batches(g, x0, nb, cores)
+    dt = time.perf_counter() - t0
+    pairs = nb * BATCH * float(g.n - 1)
+    return {"value": pairs / dt, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {nb} of {g.n // BATCH} minibatches of one iteration "
+                      f"({pairs:.3g} pairs), FP64, OpenMP over each minibatch",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step = one sampled minibatch sweep."""
+    if rank != 0:
+        return None
+    import numpy as np
+
+    from paper_2002_08233_gb300 import synth
+    g = exact_graph()
+    x0 = synth.uniform_positions(g.n, 0)
+    cores = os.cpu_count() or 1
+    nb = 4
+    for _ in range(max(args.warmup, 0)):
+        _oracle_batches(g, x0, 1, cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_batches(g, x0, nb, cores)
+    dt = time.perf_counter() - t0
+    pairs = nb * BATCH * float(g.n - 1) * args.steps
+    v = pairs / dt
+    sample = f"first {nb} minibatches of one iteration per step ({nb * BATCH * (g.n - 1):.3g} pairs)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pair-interactions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "exact BatchLayout, Barabasi-Albert n=65,536 m=4 (262,134 edges), "
+                               "minibatch 256", "n": g.n, "nnz": g.nnz, "batch": BATCH,
+                   "mode": "exact", "parallelism": "single"},
+        "cpu_baseline": {"value": v, "unit": "pair-interactions/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if rank == 0 and out is not None:
+            print(json.dumps(out))
+        return
+    out, g = run_exact(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                out["cpu_baseline"] = cpu_baseline_exact(g)
+            except Exception as e:   # the baseline is context; never fail the bench on it
+                out["cpu_baseline"] = {"error": str(e)}
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * batchlayout.h -- C ABI of a GB300-native (sm_103a) implementation of
+ * BatchLayout's force-directed layout iteration (Rahman, Sujon, Azad,
+ * "BatchLayout: A Batch-Parallel Force-Directed Graph Layout Algorithm in
+ * Shared Memory", arXiv 2002.08233).
+ *
+ * What one iteration computes (Section 2.2, Section 3.3, Algorithm 2):
+ *   for each minibatch b of BS consecutive vertex ids, in order:
+ *     for every i in b, from the same positions c:
+ *       ct_i = sum_{(i,j) in E} (|c_j-c_i|^2 / K) u_ij
+ *            + sum_{j != i, (i,j) not in E} (-R K^2 / |c_j-c_i|) u_ij,
+ *       u_ij = (c_j - c_i)/|c_j - c_i|
+ *     then c_i += Step * ct_i / |ct_i|  (no move when ct_i = 0),
+ *          Energy += |ct_i|^2
+ *   Step = 0.999^t for iteration t (Step starts at 1.0).
+ * Barnes-Hut mode (Section 3.5, Algorithms S3-S5) replaces the repulsion sum
+ * with a quadtree walk: the tree is built once per iteration over Morton-sorted
+ * positions; a node passes the acceptance test when theta > D_node/|c_i - g|
+ * and then acts with its vertex count at its centroid g.
+ *
+ * Conventions for every call:
+ *   - Status codes are returned, never abort(). bl_last_error() gives the text
+ *     of the calling thread's last failure.
+ *   - Host pointers are copied in; the caller keeps ownership. Output buffers
+ *     belong to the caller; their capacity is checked (BL_EINVAL if short).
+ *   - Handles belong to the library until the matching *_free call.
+ *   - Work is queued on the stream set by bl_set_stream (default: the legacy
+ *     default stream). Calls that return host data synchronise that stream.
+ *   - Positions are FP32, interleaved x,y (2n floats). All force arithmetic is
+ *     FP32; energies and quality metrics are accumulated in FP64.
+ *   - Device memory comes from the allocator set by bl_set_allocator
+ *     (default: cudaMalloc/cudaFree).
+ */
+#ifndef BATCHLAYOUT_H
+#define BATCHLAYOUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BL_OK = 0,
+    BL_EINVAL = 1,      /* bad argument, malformed CSR, short output buffer */
+    BL_ENOMEM = 2,      /* device or host allocation failed */
+    BL_EBUDGET = 3,     /* a request can never fit the server's memory budget */
+    BL_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+    BL_ETIMEOUT = 5,    /* a bounded device-side wait gave up (status word set) */
+    BL_EBUSY = 6,       /* object in use by queued work */
+    BL_ENOTREADY = 7,   /* serving: the result is not done yet */
+    BL_ECANCELED = 8    /* serving: the request was cancelled */
+} bl_status;
+
+typedef enum {
+    BL_EXACT = 0,       /* all-pairs repulsion (Algorithm 2) */
+    BL_BH = 1,          /* Barnes-Hut repulsion (Algorithm S5) */
+    BL_AUTO = 2         /* serving only: exact below 50,000 vertices, else BH */
+} bl_mode;
+
+/* CSR clean-up flags for bl_graph_load_csr */
+#define BL_CSR_SYMMETRIZE 1u   /* add (j,i) for every (i,j) */
+#define BL_CSR_DEDUP 2u        /* drop duplicate entries and self-loops */
+#define BL_CSR_SORT 4u         /* sort each row (implied by the two above) */
+
+typedef struct bl_graph bl_graph;
+typedef struct bl_layout bl_layout;
+typedef struct bl_server bl_server;
+
+/* Force model parameters (Section 2.2). K: optimal spring length; R: relative
+ * strength of repulsion. repulse_neighbors = 0 (default) repels non-adjacent
+ * pairs only, as the combined force f(i,c) states; 1 repels every pair j != i,
+ * as Algorithm S5's tree repulsion does literally. kahan: 1 = compensated FP32
+ * repulsion sums, 0 = plain, -1 = automatic (on for n >= 2^20). */
+typedef struct {
+    float K;
+    float R;
+    int32_t repulse_neighbors;
+    int32_t kahan;
+} bl_force_params;
+
+typedef struct {
+    int64_t iterations;          /* iterations done so far (t of the schedule) */
+    double step;                 /* Step of the next iteration = 0.999^t */
+    double energy;               /* sum |ct_i|^2 of the last iteration (FP64) */
+    double pair_interactions;    /* exact mode: n(n-1) per iteration, cumulative */
+    double vertex_updates;       /* n per iteration, cumulative */
+    double bh_far_nodes;         /* BH: accepted far-field nodes, last iteration */
+    double bh_near_pairs;        /* BH: directly summed leaf pairs, last iteration */
+    double last_run_ms;          /* device time of the last bl_layout_run */
+} bl_stats_t;
+
+/* ---- runtime configuration ------------------------------------------------ */
+
+/* Stream for all subsequent work of the calling process (a cudaStream_t cast
+ * to void*; NULL = legacy default stream). */
+bl_status bl_set_stream(void *stream);
+
+/* Device allocator hooks. alloc(bytes, ctx) returns device memory or NULL;
+ * dealloc(ptr, ctx) releases it. Pass NULLs to restore cudaMalloc/cudaFree.
+ * Objects keep the hooks they were created with. */
+bl_status bl_set_allocator(void *(*alloc)(size_t bytes, void *ctx),
+                           void (*dealloc)(void *ptr, void *ctx), void *ctx);
+
+const char *bl_last_error(void);
+const char *bl_version(void);
+
+/* ---- graph (Section 2.1: CSR rowptr[n+1], colids[nnz]) --------------------- */
+
+/* Validates and uploads an undirected graph. Without flags the CSR must be
+ * clean: rowptr[0] = 0, non-decreasing, rowptr[n] = nnz; colids in [0,n),
+ * strictly increasing within a row (no duplicates), no self-loops, symmetric.
+ * Flags repair what they name. int32 ids; n >= 1. */
+bl_status bl_graph_load_csr(int32_t n, int64_t nnz, const int32_t *rowptr,
+                            const int32_t *colids, uint32_t flags, bl_graph **out);
+bl_status bl_graph_info(const bl_graph *g, int32_t *n, int64_t *nnz);
+void bl_graph_free(bl_graph *g);
+
+/* ---- one layout ------------------------------------------------------------ */
+
+/* Creates the layout state of graph g (the graph must outlive it). Initial
+ * positions: xy (2n floats, host) when non-NULL, else uniform in [-1,1)^2 from
+ * SplitMix64 at `seed` (24 random bits per coordinate; coordinate k = 2i for
+ * x_i, 2i+1 for y_i). start_iter sets t, so Step = 0.999^start_iter (resume).
+ * params may be NULL (K = R = 1, non-neighbour repulsion, kahan automatic). */
+bl_status bl_layout_init(const bl_graph *g, const float *xy, uint64_t seed, int64_t start_iter,
+                         const bl_force_params *params, bl_layout **out);
+
+/* Replaces the positions (host, 2n floats) and the iteration counter. */
+bl_status bl_layout_set_positions(bl_layout *L, const float *xy, int64_t start_iter);
+
+/* Runs `iters` iterations with minibatch size `batch` (1 <= batch <= 8192)
+ * in mode BL_EXACT or BL_BH (theta: MAC threshold, the paper uses 1.2).
+ * Continues the step schedule from the layout's iteration counter. Queued on
+ * the stream; returns after the launch (errors of the device-side waits are
+ * reported by the next synchronising call). */
+bl_status bl_layout_run(bl_layout *L, int32_t iters, int32_t batch, bl_mode mode, float theta);
+
+/* Copies positions to host (2n floats; cap_floats >= 2n). Synchronises. */
+bl_status bl_positions(const bl_layout *L, float *xy, int64_t cap_floats);
+
+/* Device pointer of the live positions (float2[n]); valid until the next
+ * bl_layout_run or bl_layout_free. */
+bl_status bl_positions_device(const bl_layout *L, void **dptr);
+
+/* Energy of each iteration of the last bl_layout_run (FP64, Section 2.2's
+ * sum_i |f(i,c)|^2). Synchronises. *count = iterations of that run; with
+ * out == NULL only the count is returned. */
+bl_status bl_energy_history(const bl_layout *L, double *out, int64_t cap, int64_t *count);
+
+bl_status bl_stats(const bl_layout *L, bl_stats_t *out);
+void bl_layout_free(bl_layout *L);
+
+/* ---- quality (Section 3.7) --------------------------------------------------- */
+
+/* Stress (minimised over a uniform layout scale), neighbourhood preservation
+ * and edge uniformity of the current positions, accumulated in FP64 on the GPU.
+ * nsources <= 0: all-pairs stress; else that many BFS sources chosen by
+ * SplitMix64(seed) without repeats. nqueries <= 0: every vertex is an NP query;
+ * else a seeded sample. out[0..5] = {stress, scale s*, stress pairs, NP,
+ * NP queries, edge uniformity}. Synchronises. */
+bl_status bl_quality(const bl_layout *L, int32_t nsources, int32_t nqueries, uint64_t seed,
+                     double *out, int64_t cap);
+
+/* ---- many small graphs in one persistent launch ------------------------------ */
+
+/* Lays out `count` graphs with initial positions from seeds[k] (as
+ * bl_layout_init), `iters` iterations each, exact mode (BL_EXACT; BL_BH is
+ * accepted and run one graph at a time). outs[k] receives a layout handle
+ * that holds the result. One persistent kernel works through a vertex-block
+ * work list of all graphs, in chunks of iterations replayed from a captured
+ * CUDA graph. */
+bl_status bl_layout_batch(const bl_graph *const *gs, int32_t count, const uint64_t *seeds,
+                          int32_t iters, int32_t batch, bl_mode mode, float theta,
+                          bl_layout **outs);
+
+/* ---- continuous-batching server -------------------------------------------- */
+
+/* A server owns a request thread and the device memory it admits against
+ * (mem_budget_bytes of working memory). */
+bl_status bl_server_create(size_t mem_budget_bytes, bl_server **out);
+
+/* Queues a layout of g (which must stay alive until polled). mode BL_AUTO picks
+ * exact below 50,000 vertices and BH above. BL_EBUDGET if the request could
+ * never fit the budget. *ticket identifies the request. */
+bl_status bl_serve_submit(bl_server *S, const bl_graph *g, uint64_t seed, int32_t iters,
+                          int32_t batch, bl_mode mode, float theta, uint64_t *ticket);
+
+/* Non-blocking. BL_ENOTREADY until done; then copies 2n floats to xy (cap
+ * checked) and the request's latency (submit -> done, seconds) and retires it. */
+bl_status bl_serve_poll(bl_server *S, uint64_t ticket, float *xy, int64_t cap, double *latency_s);
+
+/* Cancels a queued request (BL_EBUSY once it is on the GPU). */
+bl_status bl_serve_cancel(bl_server *S, uint64_t ticket);
+
+/* out[0..5] = {completed, in flight, queued, bytes in use, p50 s, p99 s}. */
+bl_status bl_server_stats(bl_server *S, double *out, int64_t cap);
+void bl_server_free(bl_server *S);
+
+/* ---- parity hooks ------------------------------------------------------------ */
+
+/* One-snapshot forces ct_i (FP32, 2 floats per vertex) for i in [lo, hi) from
+ * the current positions, without moving any vertex: the exact engine's column
+ * and CSR phases (mode BL_EXACT) or the tree walk plus CSR attraction
+ * (mode BL_BH). f_out holds 2*(hi-lo) floats. Synchronises. */
+bl_status bl_debug_forces(bl_layout *L, bl_mode mode, float theta, int32_t lo, int32_t hi,
+                          float *f_out);
+
+/* The Barnes-Hut tree of the current positions (Section 3.5, Algorithm S3),
+ * built by the GPU: Morton codes in sorted order, the sorting permutation and
+ * the pre-order node arrays first/count/level/skip plus FP32 coordinate sums.
+ * Arrays hold `cap` nodes; *nnodes receives the node count (BL_EINVAL when cap
+ * is short, after writing *nnodes). box = {xmin, ymin, D}. Synchronises. */
+bl_status bl_debug_bh_tree(bl_layout *L, uint32_t *codes, int32_t *perm, int32_t *first,
+                           int32_t *count, int32_t *level, int32_t *skip, float *sumx,
+                           float *sumy, int64_t cap, int64_t *nnodes, float *box);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BATCHLAYOUT_H */

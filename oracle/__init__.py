@@ -51,7 +51,7 @@ def _load():
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i32, f64, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
-            lib.orc_forces.argtypes = [i32, P, P, P, f64, f64, i32, i32, f64, i32, i32, P, P]
+            lib.orc_forces.argtypes = [i32, P, P, P, f64, f64, i32, i32, f64, i32, i32, i32, P, P]
             lib.orc_run.argtypes = [i32, P, P, P, i32, i32, i32, f64, f64, f64, i32, i64, i32, P]
             lib.orc_morton.argtypes = [i32, P, P, P, P]
             lib.orc_bh_tree.argtypes = [i32, P, P, P, P, i32, P, P, P, P, P, P, P]
@@ -82,7 +82,7 @@ def _check(rc: int, what: str):
 
 
 def forces(g, xy, K=1.0, R=1.0, repulse_neighbors=False, mode=EXACT, theta=THETA_DEFAULT,
-           lo=0, hi=None):
+           lo=0, hi=None, nthreads=1):
     """One-snapshot combined forces f(i, c) for i in [lo, hi) (Section 2.2;
     BH repulsion per Algorithms S3/S4). Returns (f[hi-lo, 2], mag[hi-lo]) where
     mag_i is the sum of the magnitudes of the terms that make up f(i, c)."""
@@ -94,7 +94,7 @@ def forces(g, xy, K=1.0, R=1.0, repulse_neighbors=False, mode=EXACT, theta=THETA
     f = np.zeros((max(hi - lo, 0), 2), dtype=np.float64)
     mag = np.zeros(max(hi - lo, 0), dtype=np.float64)
     rc = lib.orc_forces(n, _ptr(rp), _ptr(ci), _ptr(x), K, R, int(repulse_neighbors), mode,
-                        theta, lo, hi, _ptr(f) if f.size else None, _ptr(mag) if mag.size else None)
+                        theta, lo, hi, nthreads, _ptr(f) if f.size else None, _ptr(mag) if mag.size else None)
     _check(rc, "forces")
     return f, mag
 

@@ -374,14 +374,23 @@ static int check_csr(int n, const int *rowptr, const int *colids)
 /* One-snapshot forces f(i, c) for i in [lo, hi), all from the same positions xy
  * (FP64, interleaved x,y). f_out[2*(i-lo)+{0,1}]; mag_out[i-lo] = sum of the
  * magnitudes of the terms that make up f(i,c). mode 0: exact, 1: BH (tree on
- * the FP32-rounded positions). */
+ * the FP32-rounded positions). nthreads > 1 spreads the vertices over OpenMP
+ * threads; results do not depend on it. */
 int orc_forces(int n, const int *rowptr, const int *colids, const double *xy,
                double K, double R, int repulse_neighbors, int mode, double theta,
-               int lo, int hi, double *f_out, double *mag_out)
+               int lo, int hi, int nthreads, double *f_out, double *mag_out)
 {
     if (check_csr(n, rowptr, colids) != ORC_OK) return ORC_EINVAL;
     if (lo < 0 || hi > n || lo > hi) return ORC_EINVAL;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
     if (mode == ORC_EXACT) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) if (nthreads > 1)
+#endif
         for (int i = lo; i < hi; i++)
             exact_force(i, n, rowptr, colids, xy, K, R, repulse_neighbors,
                         &f_out[2 * (i - lo)], &f_out[2 * (i - lo) + 1], mag_out ? &mag_out[i - lo] : NULL);
@@ -394,6 +403,9 @@ int orc_forces(int n, const int *rowptr, const int *colids, const double *xy,
     otree t;
     int rc = tree_build(&t, n, xf, yf);
     if (rc == ORC_OK) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) if (nthreads > 1)
+#endif
         for (int i = lo; i < hi; i++)
             bh_force(i, rowptr, colids, xy, &t, (float)theta, K, R, repulse_neighbors,
                      &f_out[2 * (i - lo)], &f_out[2 * (i - lo) + 1], mag_out ? &mag_out[i - lo] : NULL);

@@ -1,0 +1,268 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the public C ABI (include/batchlayout.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/batchlayout.h"
+
+namespace bl {
+
+// ---------------------------------------------------------------------------
+// host-side error plumbing
+// ---------------------------------------------------------------------------
+
+bl_status set_error(bl_status st, const std::string& msg);
+bl_status cuda_error(cudaError_t e, const char* what);
+
+#define BL_CUDA_TRY(expr)                                                  \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) return ::bl::cuda_error(e__, #expr);       \
+    } while (0)
+
+#define BL_TRY(expr)                                                       \
+    do {                                                                   \
+        bl_status s__ = (expr);                                            \
+        if (s__ != BL_OK) return s__;                                      \
+    } while (0)
+
+cudaStream_t current_stream();
+
+// device memory through the configured allocator
+struct Allocator {
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*dealloc)(void*, void*) = nullptr;
+    void* ctx = nullptr;
+};
+Allocator current_allocator();
+bl_status dev_alloc(const Allocator& a, size_t bytes, void** p);
+void dev_free(const Allocator& a, void* p);
+
+// A device buffer owned by a library object.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    Allocator a;
+    bl_status ensure(const Allocator& al, size_t need) {
+        if (need <= bytes && p) return BL_OK;
+        release();
+        a = al;
+        bl_status s = dev_alloc(a, need ? need : 16, &p);
+        if (s == BL_OK) bytes = need ? need : 16;
+        return s;
+    }
+    void release() {
+        if (p) dev_free(a, p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+int device_sm_count();
+
+// ---------------------------------------------------------------------------
+// library objects
+// ---------------------------------------------------------------------------
+
+}  // namespace bl
+
+struct bl_graph {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    std::vector<int32_t> h_rowptr, h_colids;   // host copy (CSR, cleaned)
+    bl::DevBuf rowptr, colids;                 // device copy
+};
+
+namespace bl {
+struct BHState;       // Barnes-Hut buffers (bl_bh.cu)
+void bh_state_free(BHState* s);
+}  // namespace bl
+
+struct bl_layout {
+    const bl_graph* g = nullptr;
+    bl_force_params prm{1.0f, 1.0f, 0, -1};
+    int64_t t = 0;                      // iterations done
+    bl::DevBuf pos;                     // float2[n] live positions
+    bl::DevBuf pos2;                    // float2[n] second buffer (BH sweep)
+    bl::DevBuf energy;                  // double[iters] of the last run
+    bl::DevBuf epart;                   // double energy partials
+    bl::DevBuf status;                  // int device status word + barrier counters
+    bl::DevBuf scratch;                 // forces for debug hooks
+    int64_t last_iters = 0;
+    double last_energy = 0.0;
+    double pairs = 0.0, vupd = 0.0;
+    double far_nodes = 0.0, near_pairs = 0.0;
+    double last_ms = 0.0;
+    bl::BHState* bh = nullptr;
+    bl::Allocator alloc;
+};
+
+namespace bl {
+
+// device status word values are bl_status codes
+constexpr int kMaxBatch = 8192;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
+
+// ---------------------------------------------------------------------------
+// exact engine (bl_exact.cu)
+// ---------------------------------------------------------------------------
+
+struct ExactTask {
+    int n, BS, B;
+    const int* rowptr;
+    const int* colids;
+    float2* pos;
+    double* epart;       // [iters * B * P] energy partials, or null
+    float2* f_out;       // snapshot mode: forces of all n vertices
+    int P;               // energy slots per batch
+    int iters;           // iterations in this launch (0 = snapshot mode)
+    double step0;        // Step of the first iteration
+};
+
+struct ExactParams {
+    float invK;          // 1/K
+    float negRK2;        // -R K^2
+    int repulse_neighbors;
+    int* status;         // device status word
+    unsigned* bar;       // grid barrier counter
+};
+
+// Launch shape of the grid engine: G co-resident CTAs of T threads, rpt rows per
+// thread, P energy slots per batch (CTAs that can share one batch).
+struct ExactPlan {
+    int G, T, rpt, P;
+};
+bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out);
+
+// Runs task.iters iterations (or the one-snapshot forces when iters == 0) of one
+// graph on the grid engine; stage holds 2*BS float2. Returns after queuing.
+bl_status exact_launch(const ExactPlan& plan, const ExactTask& task, const ExactParams& prm,
+                       float2* stage, cudaStream_t st);
+
+// Per-iteration energies from the partials: energy[t] = sum over batches and slots.
+bl_status energy_reduce(const double* epart, int iters, int B, int P, double* energy,
+                        cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace bl
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace bl {
+
+// Squared distance floor for coincident pairs: a pair at distance 0 contributes
+// (0,0) * (1/eps) = 0 exactly, which is the zero contribution the model gives
+// coincident vertices; for any pair farther than ~1e-15 the term is unchanged.
+#define BL_EPS2 1e-30f
+
+__device__ __forceinline__ float rcp_sfu(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    int v;
+    asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Repulsion of j on i before scaling by -R K^2: accumulates (c_j - c_i)/|c_j - c_i|^2.
+__device__ __forceinline__ void rep_pair(float xi, float yi, float xj, float yj, float& ax,
+                                         float& ay) {
+    const float dx = xj - xi;
+    const float dy = yj - yi;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
+    const float inv = rcp_sfu(d2);
+    ax = fmaf(dx, inv, ax);
+    ay = fmaf(dy, inv, ay);
+}
+
+// Kahan-compensated accumulation of v into (s, c); the sum is s - c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-wide barrier over a monotonically increasing counter, for cooperative
+// launches (all CTAs co-resident). Every wait is bounded: after kWaitLimitNs the
+// waiting CTA writes BL_ETIMEOUT to *status and every CTA leaves at its next check.
+struct GridBarrier {
+    unsigned* ctr;
+    int* status;
+    unsigned nblocks;
+    unsigned phase;
+    __device__ bool sync() {
+        __syncthreads();
+        __shared__ int s_ok;
+        phase += 1;
+        if (threadIdx.x == 0) {
+            const unsigned target = phase * nblocks;
+            __threadfence();
+            red_release_add_u32(ctr, 1u);
+            const unsigned long long t0 = global_ns();
+            int ok = 1;
+            for (unsigned spin = 0;; ++spin) {
+                const unsigned v = ld_acquire_u32(ctr);
+                if ((int)(v - target) >= 0) break;
+                if ((spin & 255u) == 255u) {
+                    if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+                    if (global_ns() - t0 > kWaitLimitNs) {
+                        atomicCAS(status, 0, (int)BL_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+};
+
+}  // namespace bl
+#endif  // __CUDACC__

@@ -1,0 +1,207 @@
+"""Exact-mode parity: the CUDA engine against the FP64 oracle on the same seeded
+inputs (Section 2.2 forces, Algorithm 2 minibatch iteration)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_08233_gb300 import synth
+from helpers import (TOL_FORCE_EXACT, TOL_POS_EXACT, force_error, oracle_sensitivity,
+                     position_error, position_tolerance)
+
+pytestmark = pytest.mark.gpu
+
+NCPU = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def core():
+    from paper_2002_08233_gb300 import core as c
+    c.load()
+    c.use_torch()
+    return c
+
+
+def _layout(core, g, xy, **kw):
+    G = core.Graph(g)
+    return G, core.Layout(G, xy=xy, **kw)
+
+
+CASES = [
+    ("grid32", lambda: synth.grid_32x32(), 0),
+    ("er777", lambda: synth.erdos_renyi(777, 6.0, 5), 7),      # ragged sizes
+    ("tree300", lambda: synth.binary_tree(300, 2), 3),
+    ("ba3000", lambda: synth.barabasi_albert(3000, 4, seed=9), 9),
+]
+
+
+@pytest.mark.parametrize("name,maker,seed", CASES)
+@pytest.mark.parametrize("rn", [False, True])
+def test_snapshot_forces_match_oracle(core, name, maker, seed, rn):
+    g = maker()
+    xy = synth.uniform_positions(g.n, seed)
+    _, L = _layout(core, g, xy, repulse_neighbors=rn)
+    f = L.debug_forces("exact")
+    ref, mag = oracle.forces(g, xy.astype(np.float64), repulse_neighbors=rn)
+    err = force_error(f, ref, mag)
+    assert err.max() <= TOL_FORCE_EXACT, (name, err.max())
+
+
+def test_snapshot_forces_nondefault_K_R(core):
+    g = synth.erdos_renyi(500, 5.0, 1)
+    xy = synth.uniform_positions(g.n, 1) * np.float32(3.0)
+    _, L = _layout(core, g, xy, K=0.7, R=2.5)
+    f = L.debug_forces("exact")
+    ref, mag = oracle.forces(g, xy.astype(np.float64), K=0.7, R=2.5)
+    assert force_error(f, ref, mag).max() <= TOL_FORCE_EXACT
+
+
+def test_snapshot_forces_evolved_layout(core):
+    """Forces on a layout the oracle has already run for 30 iterations (clusters,
+    a wide spread of distances)."""
+    g = synth.grid_32x32()
+    x0 = synth.uniform_positions(g.n, 0)
+    xe, _ = oracle.run(g, x0, iters=30, batch=128, nthreads=NCPU)
+    xe = xe.astype(np.float32)
+    _, L = _layout(core, g, xe, start_iter=30)
+    f = L.debug_forces("exact")
+    ref, mag = oracle.forces(g, xe.astype(np.float64))
+    assert force_error(f, ref, mag).max() <= TOL_FORCE_EXACT
+
+
+ITER_CASES = [
+    ("grid32_bs128", lambda: synth.grid_32x32(), 128, 0),
+    ("er777_bs100", lambda: synth.erdos_renyi(777, 6.0, 5), 100, 7),   # partial last batch
+    ("tree300_bs1", lambda: synth.binary_tree(300, 2), 1, 3),          # Algorithm 1
+    ("er200_bsall", lambda: synth.erdos_renyi(200, 4.0, 8), 4096, 8),   # one batch (Jacobi)
+    ("ba3000_bs256", lambda: synth.barabasi_albert(3000, 4, seed=9), 256, 9),
+]
+
+
+@pytest.mark.parametrize("name,maker,bs,seed", ITER_CASES)
+def test_one_iteration_positions_match_oracle(core, name, maker, bs, seed):
+    """Whole-iteration positions within max(1e-5, 4x the oracle's own one-ulp
+    input sensitivity on the same input)."""
+    g = maker()
+    xy = synth.uniform_positions(g.n, seed)
+    _, L = _layout(core, g, xy)
+    L.run(1, bs, "exact")
+    xg = L.positions()
+    xr, sens = oracle_sensitivity(g, xy, 1, bs, nthreads=NCPU)
+    _, er = oracle.run(g, xy, iters=1, batch=bs, nthreads=NCPU)
+    err = position_error(xg, xr)
+    tol = position_tolerance(TOL_POS_EXACT, sens)
+    assert err <= tol, (name, err, sens)
+    eg = L.energy_history()
+    assert eg.shape == (1,)
+    assert eg[0] == pytest.approx(er[0], rel=1e-4)
+
+
+@pytest.mark.parametrize("n,bs", [(300, 4096), (1000, 1000), (1024, 2048)])
+def test_single_batch_update_is_normalised_step(core, n, bs):
+    """With one minibatch (Jacobi), each position moves to c + Step*f/|f| with the
+    engine's own snapshot force f: checks the update arithmetic apart from the
+    force sums (FP32 rounding of c + Step*u only). For n <= 1024 the snapshot
+    hook and the run sum the same single column tile in the same order, so the
+    two forces are the same FP32 values."""
+    g = synth.erdos_renyi(n, 5.0, n)
+    xy = synth.uniform_positions(n, n)
+    _, L = _layout(core, g, xy, start_iter=40)
+    f = L.debug_forces("exact").astype(np.float64)
+    L.run(1, bs, "exact")
+    step = 0.999 ** 40
+    expect = xy + step * f / np.linalg.norm(f, axis=1)[:, None]
+    assert np.max(np.abs(L.positions() - expect)) <= 4e-7 * (1.0 + np.abs(expect).max())
+
+
+def test_step_schedule_continues_across_runs(core):
+    g = synth.erdos_renyi(400, 5.0, 3)
+    xy = synth.uniform_positions(g.n, 3)
+    _, L = _layout(core, g, xy, start_iter=17)
+    L.run(2, 64, "exact")
+    L.run(1, 64, "exact")
+    st = L.stats()
+    assert st["iterations"] == 20
+    assert st["step"] == pytest.approx(0.999 ** 20, rel=1e-12)
+    xr, sens = oracle_sensitivity(g, xy, 3, 64, start_iter=17, nthreads=NCPU)
+    assert position_error(L.positions(), xr) <= position_tolerance(TOL_POS_EXACT, sens)
+
+
+def test_every_vertex_moves_by_step(core):
+    g = synth.erdos_renyi(500, 4.0, 4)
+    xy = synth.uniform_positions(g.n, 4)
+    _, L = _layout(core, g, xy, start_iter=100)
+    L.run(1, 50, "exact")
+    moved = np.linalg.norm(L.positions().astype(np.float64) - xy, axis=1)
+    assert np.allclose(moved, 0.999 ** 100, rtol=2e-6)
+
+
+def test_edge_cases(core):
+    # a single vertex never moves; an edgeless pair repels; coincident vertices stay put
+    g1 = synth.from_edge_list(1, [])
+    _, L = _layout(core, g1, np.array([[0.25, -0.5]], np.float32))
+    L.run(3, 256, "exact")
+    assert np.array_equal(L.positions(), np.array([[0.25, -0.5]], np.float32))
+    g2 = synth.from_edge_list(2, [])
+    _, L = _layout(core, g2, np.array([[0.0, 0.0], [1.0, 0.0]], np.float32))
+    L.run(1, 2, "exact")
+    assert np.allclose(L.positions(), [[-1.0, 0.0], [2.0, 0.0]], atol=1e-6)
+    g3 = synth.from_edge_list(3, [(0, 1)])
+    xy = np.full((3, 2), 0.5, np.float32)
+    _, L = _layout(core, g3, xy)
+    assert np.array_equal(L.debug_forces("exact"), np.zeros((3, 2), np.float32))
+    L.run(1, 3, "exact")
+    assert np.array_equal(L.positions(), xy)
+
+
+def test_invalid_arguments_raise(core):
+    g = synth.grid2d(4, 4)
+    G, L = _layout(core, g, None)
+    with pytest.raises(core.BatchLayoutError):
+        L.run(1, 0, "exact")
+    with pytest.raises(core.BatchLayoutError):
+        L.run(1, 100000, "exact")
+    with pytest.raises(core.BatchLayoutError):
+        L.positions(out=np.zeros((3, 2), np.float32))
+
+
+def test_seeded_init_matches_generator(core):
+    g = synth.grid2d(10, 10)
+    G = core.Graph(g)
+    L = core.Layout(G, seed=1234)
+    assert np.array_equal(L.positions(), synth.uniform_positions(100, 1234))
+
+
+# ---- full-size workload (BA n=65,536, minibatch 256), sampled -------------------
+
+@pytest.fixture(scope="module")
+def ba65k():
+    return synth.ba_65536()
+
+
+def test_ba65536_sampled_forces(core, ba65k):
+    g = ba65k
+    xy = synth.uniform_positions(g.n, 0)
+    _, L = _layout(core, g, xy)
+    rng = np.random.default_rng(0)
+    batches = rng.choice(g.n // 256, size=4, replace=False)
+    for b in batches:
+        lo, hi = int(b) * 256, int(b) * 256 + 256
+        f = L.debug_forces("exact", lo=lo, hi=hi)
+        ref, mag = oracle.forces(g, xy.astype(np.float64), lo=lo, hi=hi)
+        assert force_error(f, ref, mag).max() <= TOL_FORCE_EXACT
+
+
+def test_ba65536_one_iteration(core, ba65k):
+    """One full iteration in the benchmark's launch configuration."""
+    g = ba65k
+    xy = synth.uniform_positions(g.n, 0)
+    _, L = _layout(core, g, xy)
+    L.run(1, 256, "exact")
+    xr, er = oracle.run(g, xy, iters=1, batch=256, nthreads=NCPU)
+    err = position_error(L.positions(), xr)
+    # one perturbed oracle run (each costs a full 4.3e9-pair iteration)
+    _, sens = oracle_sensitivity(g, xy, 1, 256, trials=1, nthreads=NCPU)
+    assert err <= position_tolerance(TOL_POS_EXACT, sens), (err, sens)
+    assert L.energy_history()[0] == pytest.approx(er[0], rel=1e-4)
