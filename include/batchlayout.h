@@ -216,6 +216,21 @@ bl_status bl_debug_bh_tree(bl_layout *L, uint32_t *codes, int32_t *perm, int32_t
                            int32_t *count, int32_t *level, int32_t *skip, float *sumx,
                            float *sumy, int64_t cap, int64_t *nnodes, float *box);
 
+/* ---- profiling hooks ---------------------------------------------------------- */
+
+/* Records device phase timestamps (global timer, ns) for the first max_steps
+ * minibatch steps of the next exact-mode bl_layout_run (0 turns it off). Per
+ * CTA and step, 12 slots: control warp {0 step start, 1 previous batch
+ * published by all CTAs, 2 column tile in shared memory, 3 bulk warps done with
+ * the previous step, 4 critical rows moved, 6 arrival posted}; bulk warps {7
+ * step start, 5 moved rows picked up, 10 neighbours staged, 8 step done};
+ * slots 9 and 11 unused (0). */
+bl_status bl_set_trace(bl_layout *L, int32_t max_steps);
+
+/* Copies the trace of the last traced run: [CTAs][max_steps][12] uint64.
+ * *count = entries; with out == NULL only the count. Synchronises. */
+bl_status bl_get_trace(const bl_layout *L, uint64_t *out, int64_t cap, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,8 @@ def _declare(lib):
         "bl_server_stats": [P, P, i64],
         "bl_debug_forces": [P, ctypes.c_int, f32, i32, i32, P],
         "bl_debug_bh_tree": [P, P, P, P, P, P, P, P, P, i64, P, P],
+        "bl_set_trace": [P, i32],
+        "bl_get_trace": [P, P, i64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name, None)
@@ -283,6 +285,18 @@ class Layout:
         out = {k: v[:m] for k, v in arrs.items()}
         out.update(codes=codes, perm=perm, sumx=sx[:m], sumy=sy[:m], nnodes=m,
                    box=tuple(float(b) for b in box))
+        return out
+
+    def set_trace(self, max_steps: int):
+        _check(_lib.bl_set_trace(self._h, int(max_steps)))
+
+    def trace(self) -> np.ndarray:
+        """Phase timestamps of the last traced run, uint64 [CTAs*steps*8]."""
+        cnt = ctypes.c_int64(0)
+        _check(_lib.bl_get_trace(self._h, None, 0, ctypes.byref(cnt)))
+        out = np.zeros(cnt.value, dtype=np.uint64)
+        if cnt.value:
+            _check(_lib.bl_get_trace(self._h, _ptr(out), out.size, ctypes.byref(cnt)))
         return out
 
     def close(self):

@@ -3,152 +3,468 @@
 // Column formulation of the minibatch sweep. Iteration t visits batches
 // k = 0..B-1 in order; batch k's force ct_i needs, for every other batch c, the
 // positions of c as they are when k is processed: updated this iteration if
-// c < k, from the previous iteration if c >= k. Equivalently, the moment batch c
-// is updated, its new positions are exactly what every row needs from c until
-// c moves again. So one global step s = (t, k):
-//   1. column phase: the positions batch k-1 received at step s-1 (a BS-vertex
-//      column tile) are added to the repulsion accumulator of every row whose
-//      next update still lies inside this launch;
-//   2. update phase: the rows of batch k now hold the repulsion of all j (their
-//      last missing column was just added); the CTAs owning them add the CSR
-//      attraction (warp per row, shuffle reduction), remove the neighbour
-//      repulsion the all-pairs sum included, and move each vertex by
-//      Step * ct/|ct| (Algorithm 2's update);
-//   3. grid barrier.
-// A prologue adds, for each row, the columns c >= batch(row) at the starting
-// positions. Over a launch every row receives every column exactly once per
-// iteration, so a launch of T iterations evaluates exactly T*n^2 pairs.
+// c < k, from the previous iteration if c >= k. So the moment batch c is updated,
+// its new positions are exactly what every row needs from c until c moves again:
+// they form a column tile that every row adds once. A prologue adds, for each
+// row, the columns c >= batch(row) at the starting positions; after that, every
+// row receives every column exactly once per iteration, so a launch of T
+// iterations evaluates exactly T*n^2 pairs.
 //
-// Rows are split evenly across CTAs (CTA ranges need not align with batches)
-// and each thread keeps its rows' positions and Kahan-compensated repulsion
-// sums in registers for the whole launch. New positions of batch k go to a
-// staging buffer (two, alternating by step) so that nothing a CTA may still
-// read as "old" is overwritten inside the step (Jacobi semantics within a batch);
-// the owners copy them into the position array one step later.
-#include <cooperative_groups.h>
+// Launch shape: one persistent cooperative CTA per SM; row i belongs to CTA
+// (i mod G), so each minibatch's rows are spread over all CTAs (about BS/G
+// "critical" rows per CTA and batch). Inside a CTA the warps specialise:
+//   - 8 bulk warps keep their rows' positions and Kahan-compensated repulsion
+//     sums in registers and only run the pair loop: at step s = (t, k) they add
+//     the column tile of batch k-1 to every row that still needs it;
+//   - one control warp runs the step chain: wait until all CTAs have published
+//     batch k-1 (monotonic counter, bounded spin), copy that column tile into
+//     shared memory, then for the CTA's rows of batch k add the tile, sum the
+//     CSR attraction and take back the neighbour repulsion, move each vertex by
+//     Step * ct/|ct| (Algorithm 2's update), publish and arrive on the counter;
+//   - the last bulk warp also stages the next rows' neighbour positions with
+//     cp.async (ids two steps ahead, positions one step ahead).
+// The roles meet at two named barriers per step (tile ready / bulk done), so the
+// latency of the step chain hides behind the bulk warps' pair work. The pair
+// loop uses packed FP32x2 arithmetic (two columns per instruction) and one SFU
+// reciprocal per pair.
+//
+// Positions are double-buffered by iteration parity: iteration t writes
+// buf[(t+1)&1] and reads not-yet-moved vertices from buf[t&1]. A CTA can lag
+// the others by at most one step, so nothing still to be read is overwritten.
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "bl_internal.cuh"
 
 namespace bl {
 
-template <int RPT, int T, class Bar>
-__device__ __forceinline__ void exact_engine(const ExactTask& tk, const ExactParams& prm, int rank,
-                                             int nrank, Bar& bar, float2* __restrict__ stage) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = tk.n, BS = tk.BS, B = tk.B;
-    float4* s_col = reinterpret_cast<float4*>(smem);            // ceil(BS/2) float4
-    float4* s_row = s_col + ((BS + 1) >> 1);                     // BS float4
-    double* s_e = reinterpret_cast<double*>(s_row + BS);         // T/32 doubles
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-    const int rows_per = (n + nrank - 1) / nrank;
-    const int r0 = min(n, rank * rows_per);
-    const int r1 = min(n, r0 + rows_per);
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    constexpr int W = T / 32;
-    const bool snapshot = tk.iters == 0;
-    const bool rn = prm.repulse_neighbors != 0;
-
-    float xi[RPT], yi[RPT], sx[RPT], sy[RPT], cx[RPT], cy[RPT];
-    int bi[RPT];
-#pragma unroll
-    for (int m = 0; m < RPT; m++) {
-        const int i = r0 + tid + m * T;
-        const bool v = i < r1;
-        const float2 p = v ? __ldcg(&tk.pos[i]) : make_float2(0.f, 0.f);
-        xi[m] = p.x;
-        yi[m] = p.y;
-        sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
-        bi[m] = v ? i / BS : -1;
+// CSR terms of one neighbour: attraction (d^2/K) (c_j - c_i)/d = (d/K)(c_j - c_i),
+// and, unless repulse_neighbors, the repulsion term the all-pairs sum gave this
+// neighbour, computed with exactly rep_pair's expressions so that it cancels.
+__device__ __forceinline__ void edge_terms(float xi, float yi, float2 p, float invK, bool rn,
+                                           float& ax, float& ay, float& qx, float& qy) {
+    const float dx = p.x - xi;
+    const float dy = p.y - yi;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
+    const float a = d2 * rsqrt_sfu(d2) * invK;
+    ax = fmaf(dx, a, ax);
+    ay = fmaf(dy, a, ay);
+    if (!rn) {
+        const float inv = rcp_sfu(d2);
+        qx = fmaf(dx, inv, qx);
+        qy = fmaf(dy, inv, qy);
     }
-    if (r0 >= r1 && snapshot) return;   // nothing owned, nothing to wait for
-    const int b_first = r0 < r1 ? r0 / BS : B;      // first batch with a row here
-    const int b_last = r0 < r1 ? (r1 - 1) / BS : -1;
+}
 
-    // ---- column tile: load BS positions into shared memory --------------------
-    auto load_col = [&](const float2* src, int nc) {
-        for (int q = tid; q < (nc + 1) / 2; q += T) {
-            const float2 a = __ldcg(&src[2 * q]);
-            const float2 b = (2 * q + 1 < nc) ? __ldcg(&src[2 * q + 1]) : make_float2(0.f, 0.f);
-            s_col[q] = make_float4(a.x, a.y, b.x, b.y);
-        }
+// ---- packed FP32x2 arithmetic (two columns per instruction) -----------------------
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+// Column tiles are stored in pairs: float4 q = (x_2q, x_2q+1, y_2q, y_2q+1).
+// The pair loop: rows m in [mlo, mhi) of the thread against the tile's first
+// 2*np columns; (XI, YI) hold each row's coordinates twice, (AX, AY) two partial
+// sums per row. mlo/mhi are warp-uniform, so skipped rows cost no SFU work.
+template <int RPT>
+__device__ __forceinline__ void tile_pairs2(const float4* __restrict__ tile, int np, int mlo,
+                                            int mhi, const f32x2 (&XI)[RPT],
+                                            const f32x2 (&YI)[RPT], f32x2 (&AX)[RPT],
+                                            f32x2 (&AY)[RPT]) {
+    const f32x2 E = pk2(BL_EPS2, BL_EPS2);
+    auto pair2 = [&](const f32x2 X, const f32x2 Y, int m) {
+        f32x2 dx, dy, d2;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(XI[m]));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(YI[m]));
+        asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d2) : "l"(dy), "l"(E));
+        asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d2) : "l"(dx), "l"(d2));
+        float da, db;
+        upk2(d2, da, db);
+        const f32x2 inv = pk2(rcp_sfu(da), rcp_sfu(db));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(AX[m]) : "l"(dx), "l"(inv));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(AY[m]) : "l"(dy), "l"(inv));
     };
-    // ---- pair loop over the staged tile; adds to rows flagged in `need` --------
-    auto accumulate = [&](int nc, const bool (&need)[RPT]) {
-        float ax[RPT], ay[RPT];
-#pragma unroll
-        for (int m = 0; m < RPT; m++) ax[m] = ay[m] = 0.f;
-        const int np = nc >> 1;
+    if (mlo == 0 && mhi == RPT) {   // every row: no predicate in the loop
 #pragma unroll 4
         for (int q = 0; q < np; q++) {
-            const float4 p = s_col[q];
+            const float4 p = tile[q];
+            const f32x2 X = pk2(p.x, p.y), Y = pk2(p.z, p.w);
 #pragma unroll
-            for (int m = 0; m < RPT; m++) {
-                rep_pair(xi[m], yi[m], p.x, p.y, ax[m], ay[m]);
-                rep_pair(xi[m], yi[m], p.z, p.w, ax[m], ay[m]);
-            }
+            for (int m = 0; m < RPT; m++) pair2(X, Y, m);
         }
-        if (nc & 1) {
-            const float4 p = s_col[np];
-#pragma unroll
-            for (int m = 0; m < RPT; m++) rep_pair(xi[m], yi[m], p.x, p.y, ax[m], ay[m]);
-        }
+        return;
+    }
+#pragma unroll 4
+    for (int q = 0; q < np; q++) {
+        const float4 p = tile[q];
+        const f32x2 X = pk2(p.x, p.y), Y = pk2(p.z, p.w);
 #pragma unroll
         for (int m = 0; m < RPT; m++)
-            if (need[m]) {
-                kahan_add(sx[m], cx[m], ax[m]);
-                kahan_add(sy[m], cy[m], ay[m]);
-            }
-    };
-    // ---- update phase for the rows of batch k in [r0, r1) ------------------------
-    // prev_lo/prev_n: the batch updated one step earlier, whose new positions are
-    // read from prev_stage instead of the position array. Returns false on error.
-    auto update_batch = [&](int k, float stepf, const float2* prev_stage, int prev_lo, int prev_n,
-                            float2* out_stage, double* e_slot) {
-        const int blo = max(r0, k * BS), bhi = min(r1, (k + 1) * BS);
-        if (blo >= bhi) return;   // CTA-uniform
+            if (m >= mlo && m < mhi) pair2(X, Y, m);
+    }
+}
+
+// warp-uniform range [mlo, mhi) covering every m flagged in need[] by any lane
+template <int RPT>
+__device__ __forceinline__ void need_range(const bool (&need)[RPT], int& mlo, int& mhi) {
+    int lo = RPT, hi = 0;
+#pragma unroll
+    for (int m = 0; m < RPT; m++)
+        if (need[m]) {
+            lo = min(lo, m);
+            hi = m + 1;
+        }
+    mlo = (int)__reduce_min_sync(0xffffffffu, (unsigned)lo);
+    mhi = (int)__reduce_max_sync(0xffffffffu, (unsigned)hi);
+}
+
+// Shared-memory carve-up (bytes); the host sizes the launch with the same code.
+struct EngineSmem {
+    int tile, pos, rpl, rpe, crep, off, cid, nbr, ctl, total;
+    __host__ __device__ EngineSmem(int BS, int nloc, int CR, int CAP, int NW) {
+        const int TQ = (BS + 1) / 2;
+        tile = 0;                                        // 2 x TQ float4: column tiles
+        pos = tile + 2 * TQ * 16;                        // nloc float2: local positions
+        rpl = pos + ((nloc * 8 + 15) / 16) * 16;         // nloc int: rowptr[i]
+        rpe = rpl + ((nloc * 4 + 15) / 16) * 16;         // nloc int: rowptr[i+1]
+        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 x CR float2: critical sums
+        off = crep + ((2 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
+        cid = off + ((3 * (CR + 1) * 4 + 15) / 16) * 16; // 3 x CAP int: staged column ids
+        nbr = cid + 3 * CAP * 4;                         // 2 x CAP float2: staged positions
+        ctl = nbr + 2 * CAP * 8;                         // control words
+        total = ctl + 64;
+    }
+};
+
+// critical rows of batch k in CTA `rank`: local indices [lo, hi)
+__device__ __forceinline__ void crit_range(int k, int BS, int n, int rank, int G, int& lo,
+                                           int& hi) {
+    const int a = k * BS - rank;
+    const int b = min((k + 1) * BS, n) - rank;
+    lo = a > 0 ? (a + G - 1) / G : 0;
+    hi = b > 0 ? (b + G - 1) / G : 0;
+    if (hi < lo) hi = lo;
+}
+
+// Named CTA barriers between the warp roles. The non-aligned forms count
+// threads, and each call site first reconverges its warp.
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+    __syncwarp();
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int count) {
+    __syncwarp();
+    asm volatile("barrier.cta.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+constexpr int kBarTile = 1;   // control warp -> bulk warps: tile of step s ready
+constexpr int kBarDone = 2;   // bulk warps -> control warp: step s finished
+constexpr int kCritLanes = 4; // critical rows the control warp finishes together
+
+// phase timestamp (global timer, ns) of step s, slot q, when tracing
+__device__ __forceinline__ void trace_mark(const ExactTask& tk, int rank, int s, int q) {
+    if (tk.trace != nullptr && s < tk.trace_steps)
+        tk.trace[((size_t)rank * tk.trace_steps + s) * kTraceSlots + q] = global_ns();
+}
+
+// column q of a paired tile
+__device__ __forceinline__ float2 tile_col(const float4* tile, int q) {
+    const float4 p = tile[q >> 1];
+    return (q & 1) ? make_float2(p.y, p.w) : make_float2(p.x, p.z);
+}
+
+template <int RPT, int TB>
+__global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, ExactParams prm) {
+    constexpr int T = TB + 32;
+    constexpr int NW = TB / 32;   // bulk warps
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = gridDim.x, rank = blockIdx.x;
+    const int n = tk.n, BS = tk.BS, B = tk.B;
+    const int CR = tk.crit_cap, CAP = tk.nbr_cap;
+    const int nloc = n > rank ? (n - rank + G - 1) / G : 0;
+    const EngineSmem L(BS, (n + G - 1) / G, CR, CAP, NW);
+    const int TQ = (BS + 1) / 2;
+    float4* s_tile = reinterpret_cast<float4*>(smem + L.tile);
+    float2* s_pos = reinterpret_cast<float2*>(smem + L.pos);
+    int* s_rpl = reinterpret_cast<int*>(smem + L.rpl);
+    int* s_rpe = reinterpret_cast<int*>(smem + L.rpe);
+    float2* s_crep = reinterpret_cast<float2*>(smem + L.crep);
+    int* s_off = reinterpret_cast<int*>(smem + L.off);
+    int* s_cid = reinterpret_cast<int*>(smem + L.cid);
+    float2* s_nbr = reinterpret_cast<float2*>(smem + L.nbr);
+    volatile int* s_ctl = reinterpret_cast<volatile int*>(smem + L.ctl);
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool is_ctl = tid < 32;
+    const int tb = tid - 32;                 // bulk thread index
+    const int wb = tb >> 5;                  // bulk warp index
+    const bool is_stager = wb == NW - 1;     // bulk warp that stages neighbours
+    const bool snapshot = tk.iters == 0;
+    const bool rn = prm.repulse_neighbors != 0;
+    const float invK = prm.invK, negRK2 = prm.negRK2;
+    float2* const buf0 = tk.pos;
+    float2* const buf1 = tk.pos_alt;
+
+    // ---- bulk state: blocks of 32 consecutive local rows per warp (so a warp's rows
+    //      share few minibatches and whole warps skip columns they do not need);
+    //      blocks go first to the warps that do not share a sub-partition with the
+    //      control warp (hardware warp w runs on sub-partition w % 4) -------------------
+    const int wslot = (wb + 1) % 4 == 0 ? (NW / 4) * 3 + wb / 4
+                                         : ((wb + 1) % 4 - 1) + 3 * (wb / 4);
+    f32x2 XI[RPT], YI[RPT];
+    float sx[RPT], sy[RPT], cx[RPT], cy[RPT];
+    int bi[RPT], lrow[RPT];
+#pragma unroll
+    for (int m = 0; m < RPT; m++) {
+        const int li = lane + 32 * (wslot + NW * m);
+        const bool v = !is_ctl && li < nloc;
+        const int i = rank + G * li;
+        const float2 p = v ? __ldcg(&buf0[i]) : make_float2(0.f, 0.f);
+        XI[m] = pk2(p.x, p.x);
+        YI[m] = pk2(p.y, p.y);
+        sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
+        bi[m] = v ? i / BS : -1;
+        lrow[m] = li;
+    }
+    for (int li = tid; li < nloc; li += T) {
+        const int i = rank + G * li;
+        s_pos[li] = __ldcg(&buf0[i]);
+        s_rpl[li] = __ldg(&tk.rowptr[i]);
+        s_rpe[li] = __ldg(&tk.rowptr[i + 1]);
+    }
+    if (tid == 0) s_ctl[0] = 0;
+
+    // pair loop + tail + Kahan for the flagged rows against a paired tile of nc columns
+    auto add_tile = [&](const float4* tile, int nc, const bool (&need)[RPT]) {
+        int mlo, mhi;
+        need_range<RPT>(need, mlo, mhi);
+        if (mlo >= mhi) return;
+        f32x2 AX[RPT], AY[RPT];
+#pragma unroll
+        for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
+        tile_pairs2<RPT>(tile, nc >> 1, mlo, mhi, XI, YI, AX, AY);
 #pragma unroll
         for (int m = 0; m < RPT; m++) {
-            const int i = r0 + tid + m * T;
-            if (i >= blo && i < bhi)
-                s_row[i - blo] = make_float4(xi[m], yi[m], sx[m] - cx[m], sy[m] - cy[m]);
+            float a0, a1, b0, b1, xi, yi, dummy;
+            upk2(AX[m], a0, a1);
+            upk2(AY[m], b0, b1);
+            upk2(XI[m], xi, dummy);
+            upk2(YI[m], yi, dummy);
+            float ax = a0 + a1, ay = b0 + b1;
+            if (nc & 1) {
+                const float2 pc = tile_col(tile, nc - 1);
+                rep_pair(xi, yi, pc.x, pc.y, ax, ay);
+            }
+            if (need[m]) {
+                kahan_add(sx[m], cx[m], ax);
+                kahan_add(sy[m], cy[m], ay);
+            }
+        }
+    };
+    // tile of column c into buffer dst (paired layout), threads [t0, t0+nt) copying
+    auto copy_tile = [&](float4* dst, const float2* src, int nc, int t, int nt) {
+        for (int q = t; q < (nc + 1) / 2; q += nt) {
+            const float2 a = __ldcg(&src[2 * q]);
+            const float2 b = (2 * q + 1 < nc) ? __ldcg(&src[2 * q + 1]) : make_float2(0.f, 0.f);
+            dst[q] = make_float4(a.x, b.x, a.y, b.y);
+        }
+    };
+
+    // ---- prologue: columns c >= batch(row) at the starting positions (every
+    //      column in snapshot mode); the next tile is fetched into registers while
+    //      the bulk warps add the current one -----------------------------------------
+    {
+        const bool one_each = TQ <= T;
+        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto fetch = [&](int c) {
+            const int nc = min(BS, n - c * BS);
+            const float2* src = buf0 + (size_t)c * BS;
+            if (tid < (nc + 1) / 2) {
+                const float2 a = __ldcg(&src[2 * tid]);
+                const float2 b = (2 * tid + 1 < nc) ? __ldcg(&src[2 * tid + 1]) : make_float2(0.f, 0.f);
+                nxt = make_float4(a.x, b.x, a.y, b.y);
+            }
+        };
+        if (one_each) fetch(0);
+        for (int c = 0; c < B; c++) {
+            const int nc = min(BS, n - c * BS);
+            float4* tile = s_tile + (size_t)(c & 1) * TQ;
+            if (one_each) {
+                if (tid < (nc + 1) / 2) tile[tid] = nxt;
+                __syncthreads();
+                if (c + 1 < B) fetch(c + 1);
+            } else {
+                copy_tile(tile, buf0 + (size_t)c * BS, nc, tid, T);
+                __syncthreads();
+            }
+            if (!is_ctl) {
+                bool need[RPT];
+#pragma unroll
+                for (int m = 0; m < RPT; m++) need[m] = bi[m] >= 0 && (snapshot || bi[m] <= c);
+                add_tile(tile, nc, need);
+            }
+            if (!one_each) __syncthreads();
         }
         __syncthreads();
-        double e_acc = 0.0;
-        for (int r = blo + warp; r < bhi; r += W) {
-            const float4 me = s_row[r - blo];
-            float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
-            const int e0 = __ldg(&tk.rowptr[r]), e1 = __ldg(&tk.rowptr[r + 1]);
-            for (int e = e0 + lane; e < e1; e += 32) {
-                const int j = __ldg(&tk.colids[e]);
-                const unsigned pj_off = (unsigned)(j - prev_lo);
-                const float2 pj = pj_off < (unsigned)prev_n ? __ldcg(&prev_stage[pj_off])
-                                                            : __ldcg(&tk.pos[j]);
-                const float dx = pj.x - me.x;
-                const float dy = pj.y - me.y;
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-                // attraction (d^2/K) * (c_j - c_i)/d = (d/K) (c_j - c_i)
-                const float a = d2 * rsqrt_sfu(d2) * prm.invK;
-                ax = fmaf(dx, a, ax);
-                ay = fmaf(dy, a, ay);
-                if (!rn) {   // the all-pairs sum repelled this neighbour: take it back
-                    const float inv = rcp_sfu(d2);
-                    qx = fmaf(dx, inv, qx);
-                    qy = fmaf(dy, inv, qy);
+    }
+
+    // bulk: post the sums of the rows of batch kk into crep and restart them
+    auto post_rows = [&](int kk, float2* crep) {
+        int lo, hi;
+        crit_range(kk, BS, n, rank, G, lo, hi);
+#pragma unroll
+        for (int m = 0; m < RPT; m++) {
+            const int li = lrow[m];
+            if (bi[m] == kk && li >= lo && li < hi) {
+                crep[li - lo] = make_float2(sx[m] - cx[m], sy[m] - cy[m]);
+                sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
+            }
+        }
+    };
+
+    // ---- neighbour staging (one warp) -----------------------------------------------
+    // column ids of the edges of batch kk's rows into id slot `slot` (async)
+    auto stage_ids = [&](int kk, int slot) {
+        int lo, hi;
+        crit_range(kk, BS, n, rank, G, lo, hi);
+        int* off = s_off + slot * (CR + 1);
+        int* cid = s_cid + (size_t)slot * CAP;
+        if (lane == 0) {
+            int acc = 0;
+            for (int c = 0; c < hi - lo; c++) {
+                off[c] = acc;
+                acc += s_rpe[lo + c] - s_rpl[lo + c];
+            }
+            off[hi - lo] = acc;
+        }
+        __syncwarp();
+        const int tot = min(off[hi - lo], CAP);
+        int c = 0;
+        for (int f = lane; f < tot; f += 32) {
+            while (off[c + 1] <= f) c++;
+            cp_async4(&cid[f], &tk.colids[s_rpl[lo + c] + (f - off[c])]);
+        }
+        cp_async_commit();
+    };
+    // positions of those neighbours (ids in `slot`, landed) into position slot
+    // `pslot`, as the step of batch kk reads them (bnew/bold: that step's buffers):
+    // batch(j) < kk moved in this iteration (bnew), batch(j) >= kk not yet (bold);
+    // batch kprev comes from the column tile instead (kprev < 0: no tile)
+    auto stage_pos = [&](int kk, int kprev, int slot, int pslot, const float2* bnew,
+                         const float2* bold) {
+        int lo, hi;
+        crit_range(kk, BS, n, rank, G, lo, hi);
+        const int* off = s_off + slot * (CR + 1);
+        const int* cid = s_cid + (size_t)slot * CAP;
+        float2* nbr = s_nbr + (size_t)pslot * CAP;
+        const int tot = min(off[hi - lo], CAP);
+        for (int f = lane; f < tot; f += 32) {
+            const int j = cid[f];
+            const int bj = j / BS;
+            if (kprev >= 0 && bj == kprev) continue;
+            cp_async8(&nbr[f], bj < kk ? bnew + j : bold + j);
+        }
+        cp_async_commit();
+    };
+
+    // ---- control warp: finish the rows of batch k --------------------------------------
+    // Rows kCritLanes at a time. Column kprev: 8 lanes per row over the tile, then a
+    // 3-level butterfly inside each 8-lane group. CSR: one lane per row (rows with
+    // more than 32 edges: the whole warp). Lane r then moves row r (or records the
+    // snapshot force). Returns this lane's energy contribution.
+    auto ctl_critical = [&](int k, int kprev, int slot, int pslot, const float4* tile,
+                            float stepf, const float2* bnew, const float2* bold,
+                            const float2* crep, float2* out) -> double {
+        int lo, hi;
+        crit_range(k, BS, n, rank, G, lo, hi);
+        const int* off = s_off + slot * (CR + 1);
+        const int* cid = s_cid + (size_t)slot * CAP;
+        const float2* nbr = s_nbr + (size_t)pslot * CAP;
+        const int kplo = kprev >= 0 ? kprev * BS : 0;
+        const int kpn = kprev >= 0 ? min(BS, n - kplo) : 0;
+        auto nbr_pos = [&](int c, int ee, int e0) -> float2 {
+            const int f = off[c] + (ee - e0);
+            const int j = f < CAP ? cid[f] : __ldg(&tk.colids[ee]);
+            const unsigned o = (unsigned)(j - kplo);
+            if (o < (unsigned)kpn) return tile_col(tile, (int)o);
+            if (f < CAP) return nbr[f];
+            return __ldcg(j < k * BS ? bnew + j : bold + j);
+        };
+        double e = 0.0;
+        for (int c0 = 0; c0 < hi - lo; c0 += kCritLanes) {
+            const int nr = min(kCritLanes, hi - lo - c0);
+            // column kprev: lane group g = lane / 8 takes row c0 + g
+            const int g = lane >> 3, gl = lane & 7;
+            float rx = 0.f, ry = 0.f;
+            if (g < nr) {
+                const float2 me = s_pos[lo + c0 + g];
+                for (int q = gl; q < kpn; q += 8) {
+                    const float2 pc = tile_col(tile, q);
+                    rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
                 }
             }
-            ax = warp_sum(ax);
-            ay = warp_sum(ay);
-            qx = warp_sum(qx);
-            qy = warp_sum(qy);
-            if (lane == 0) {
-                const float fx = fmaf(prm.negRK2, me.z - qx, ax);
-                const float fy = fmaf(prm.negRK2, me.w - qy, ay);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                rx += __shfl_xor_sync(0xffffffffu, rx, o);
+                ry += __shfl_xor_sync(0xffffffffu, ry, o);
+            }
+            // hub rows: whole-warp CSR sums
+            float hax = 0.f, hay = 0.f, hqx = 0.f, hqy = 0.f;
+            for (int r = 0; r < nr; r++) {
+                const int li = lo + c0 + r;
+                const int e0 = s_rpl[li], e1 = s_rpe[li];
+                if (e1 - e0 <= 32) continue;   // warp-uniform
+                const float2 me = s_pos[li];
+                float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
+                for (int ee = e0 + lane; ee < e1; ee += 32)
+                    edge_terms(me.x, me.y, nbr_pos(c0 + r, ee, e0), invK, rn, ax, ay, qx, qy);
+                ax = warp_sum(ax);
+                ay = warp_sum(ay);
+                qx = warp_sum(qx);
+                qy = warp_sum(qy);
+                if (lane == r) {
+                    hax = ax; hay = ay; hqx = qx; hqy = qy;
+                }
+            }
+            // lane r finishes row c0 + r; its column sum sits in lane group r
+            const float rxs = __shfl_sync(0xffffffffu, rx, (lane & 3) * 8);
+            const float rys = __shfl_sync(0xffffffffu, ry, (lane & 3) * 8);
+            if (lane < nr) {
+                const int c = c0 + lane;
+                const int li = lo + c;
+                const int i = rank + G * li;
+                const float2 me = s_pos[li];
+                const int e0 = s_rpl[li], e1 = s_rpe[li];
+                float ax = hax, ay = hay, qx = hqx, qy = hqy;
+                if (e1 - e0 <= 32)
+                    for (int ee = e0; ee < e1; ee++)
+                        edge_terms(me.x, me.y, nbr_pos(c, ee, e0), invK, rn, ax, ay, qx, qy);
+                float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
+                if (kprev >= 0) {
+                    kahan_add(sxr, cxr, rxs);
+                    kahan_add(syr, cyr, rys);
+                }
+                const float fx = fmaf(negRK2, (sxr - cxr) - qx, ax);
+                const float fy = fmaf(negRK2, (syr - cyr) - qy, ay);
                 if (snapshot) {
-                    tk.f_out[r] = make_float2(fx, fy);
+                    out[i] = make_float2(fx, fy);
                 } else {
                     float nx = me.x, ny = me.y;
                     float gx = fx, gy = fy;
@@ -163,128 +479,171 @@ __device__ __forceinline__ void exact_engine(const ExactTask& tk, const ExactPar
                         nx = fmaf(sc, gx, me.x);
                         ny = fmaf(sc, gy, me.y);
                     }
-                    out_stage[r - k * BS] = make_float2(nx, ny);
-                    s_row[r - blo].x = nx;
-                    s_row[r - blo].y = ny;
-                    e_acc += (double)fx * (double)fx + (double)fy * (double)fy;
+                    out[i] = make_float2(nx, ny);
+                    s_pos[li] = make_float2(nx, ny);
+                    e += (double)fmaf(fx, fx, fy * fy);   // |ct|^2 in FP32, summed in FP64
                 }
             }
+            __syncwarp();
         }
-        if (lane == 0) s_e[warp] = e_acc;
-        __syncthreads();
-        if (tid == 0 && e_slot != nullptr) {
-            double e = 0.0;
-            for (int w = 0; w < W; w++) e += s_e[w];
-            *e_slot = e;
-        }
-#pragma unroll
-        for (int m = 0; m < RPT; m++) {
-            const int i = r0 + tid + m * T;
-            if (i >= blo && i < bhi) {
-                if (!snapshot) {
-                    const float4 v = s_row[i - blo];
-                    xi[m] = v.x;
-                    yi[m] = v.y;
-                }
-                sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
-            }
-        }
-        __syncthreads();
+        return e;
     };
 
-    // ---- prologue: columns c >= batch(row) at the starting positions (every column
-    //      in snapshot mode) ---------------------------------------------------------
-    {
-        bool need[RPT];
-        for (int c = snapshot ? 0 : b_first; c < B; c++) {
-            const int nc = min(BS, n - c * BS);
-#pragma unroll
-            for (int m = 0; m < RPT; m++) need[m] = bi[m] >= 0 && (snapshot || bi[m] <= c);
-            load_col(tk.pos + (size_t)c * BS, nc);
+    if (snapshot) {
+        for (int k = 0; k < B; k++) {
+            if (!is_ctl) post_rows(k, s_crep);
+            if (is_stager) {
+                stage_ids(k, 0);
+                cp_async_wait_all();
+                __syncwarp();
+                stage_pos(k, -1, 0, 0, buf0, buf0);
+                cp_async_wait_all();
+                __syncwarp();
+            }
             __syncthreads();
-            accumulate(nc, need);
+            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out);
             __syncthreads();
         }
-    }
-    if (snapshot) {
-        // every row now holds the repulsion of all j at the same positions
-        for (int k = b_first; k <= b_last; k++)
-            update_batch(k, 0.f, nullptr, 0, 0, nullptr, nullptr);
         return;
     }
-    if (!bar.sync()) return;   // nobody moves before every prologue has read
 
-    // ---- main loop over global steps ------------------------------------------------
+    // ---- main loop ---------------------------------------------------------------------
     const int S = tk.iters * B;
-    double step = tk.step0;
-    int prev_k = -1;
-    for (int s = 0; s < S; s++) {
-        const int it = s / B;
-        const int k = s - it * B;
-        if (k == 0 && s > 0) step *= 0.999;   // Algorithm 2: Step = Step * 0.999
-        const float2* prev_stage = stage + (size_t)((s + 1) & 1) * BS;   // written at s-1
-        float2* cur_stage = stage + (size_t)(s & 1) * BS;
-        int prev_lo = 0, prev_n = 0;
-        if (s > 0) {
-            prev_lo = prev_k * BS;
-            prev_n = min(BS, n - prev_lo);
-            // owners make the position array current for the batch moved at s-1
-#pragma unroll
-            for (int m = 0; m < RPT; m++)
-                if (bi[m] == prev_k) tk.pos[r0 + tid + m * T] = make_float2(xi[m], yi[m]);
-            // column phase: does any row here still need column prev_k in this launch?
-            const bool last_iter = (it + 1 == tk.iters);
-            const bool any = !last_iter || (b_last >= k);
-            if (any && r0 < r1) {
-                bool need[RPT];
-#pragma unroll
-                for (int m = 0; m < RPT; m++) need[m] = bi[m] >= 0 && (!last_iter || bi[m] >= k);
-                load_col(prev_stage, prev_n);
-                __syncthreads();
-                accumulate(prev_n, need);
-                __syncthreads();
+    const unsigned Gu = (unsigned)G;
+    if (!is_ctl) post_rows(0, s_crep);   // batch 0's sums for step 0
+    if (is_stager) {                     // ids of steps 0 and 1, positions of step 0
+        stage_ids(0, 0);
+        if (S > 1) stage_ids(1 % B, 1);
+        cp_async_wait_all();
+        __syncwarp();
+        stage_pos(0, -1, 0, 0, buf1, buf0);
+        cp_async_wait_all();
+        __syncwarp();
+    }
+    __syncthreads();
+
+    if (is_ctl) {
+        double step = tk.step0;
+        double e_iter = 0.0;
+        for (int s = 0; s < S; s++) {
+            const int it = s / B;
+            const int k = s - it * B;
+            if (k == 0 && s > 0) step *= 0.999;   // Algorithm 2: Step = Step * 0.999
+            const float2* bold = (it & 1) ? buf1 : buf0;
+            float2* bnew = (it & 1) ? buf0 : buf1;
+            const int kprev = s > 0 ? (k + B - 1) % B : -1;
+            float4* tile = s_tile + (size_t)(s & 1) * TQ;
+            if (lane == 0) trace_mark(tk, rank, s, 0);
+            if (s > 0) {
+                // wait until every CTA has published batch kprev (bounded)
+                int ok = 1;
+                if (lane == 0) {
+                    const unsigned target = (unsigned)s * Gu;
+                    const unsigned long long t0 = global_ns();
+                    for (unsigned spin = 0;; ++spin) {
+                        if ((int)(ld_acquire_u32(prm.bar) - target) >= 0) break;
+                        if ((spin & 255u) == 255u) {
+                            if (ld_volatile_i32(prm.status) != 0) { ok = 0; break; }
+                            if (global_ns() - t0 > kWaitLimitNs) {
+                                atomicCAS(prm.status, 0, (int)BL_ETIMEOUT);
+                                ok = 0;
+                                break;
+                            }
+                        }
+                    }
+                    trace_mark(tk, rank, s, 1);
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();   // lane 0's acquire orders the other lanes' loads
+                if (!ok) {
+                    s_ctl[0] = 1;                 // tell the bulk warps to leave
+                    bar_sync_n(kBarDone, T);      // their step s-1 is over
+                    bar_arrive_n(kBarTile, T);
+                    return;
+                }
+                // the buffer batch kprev was written to at step s-1
+                const float2* bprev = (k == 0) ? bold : bnew;
+                copy_tile(tile, bprev + (size_t)kprev * BS, min(BS, n - kprev * BS), lane, 32);
+                __syncwarp();
+            }
+            if (lane == 0) trace_mark(tk, rank, s, 2);
+            if (s > 0) bar_sync_n(kBarDone, T);   // bulk finished step s-1
+            if (lane == 0) trace_mark(tk, rank, s, 3);
+            bar_arrive_n(kBarTile, T);            // bulk may start step s
+            const double e = ctl_critical(k, kprev, s % 3, s & 1, tile, (float)step, bnew, bold,
+                                          s_crep + (size_t)(s & 1) * CR, bnew);
+            if (lane == 0) trace_mark(tk, rank, s, 4);
+            e_iter += e;
+            __syncwarp();
+            if (lane == 0) {
+                red_release_add_u32(prm.bar, 1u);   // this CTA's part of batch k is out
+                trace_mark(tk, rank, s, 6);
+            }
+            if (k == B - 1) {
+                const double et = warp_sum_d(e_iter);   // fixed butterfly over lanes
+                if (lane == 0 && tk.e_iter != nullptr) tk.e_iter[(size_t)it * G + rank] = et;
+                e_iter = 0.0;
             }
         }
-        if (k >= b_first && k <= b_last) {
-            const int slot = rank - (k * BS) / rows_per;
-            double* e_slot = tk.epart ? tk.epart + ((size_t)s * tk.P + slot) : nullptr;
-            update_batch(k, (float)step, prev_stage, prev_lo, prev_n, cur_stage, e_slot);
-        }
-        prev_k = k;
-        if (!bar.sync()) return;
-    }
-    // the last batch's owners publish its positions
+        bar_sync_n(kBarDone, T);   // the bulk warps' last step
+    } else {
+        for (int s = 0; s < S; s++) {
+            const int it = s / B;
+            const int k = s - it * B;
+            const int kprev = s > 0 ? (k + B - 1) % B : -1;
+            const int kpn = kprev >= 0 ? min(BS, n - kprev * BS) : 0;
+            bar_sync_n(kBarTile, T);
+            if (s_ctl[0]) return;
+            if (tb == 0) trace_mark(tk, rank, s, 7);
+            const float4* tile = s_tile + (size_t)(s & 1) * TQ;
+            // rows moved at step s-1 by the control warp
 #pragma unroll
-    for (int m = 0; m < RPT; m++)
-        if (bi[m] == prev_k) tk.pos[r0 + tid + m * T] = make_float2(xi[m], yi[m]);
+            for (int m = 0; m < RPT; m++)
+                if (s > 0 && bi[m] == kprev) {
+                    const float2 p = s_pos[lrow[m]];
+                    XI[m] = pk2(p.x, p.x);
+                    YI[m] = pk2(p.y, p.y);
+                }
+            if (tb == 0) trace_mark(tk, rank, s, 5);
+            if (is_stager && s + 1 < S) {   // neighbours of step s+1, ids of step s+2
+                const int kn = (k + 1) % B;
+                const int itn = kn == 0 ? it + 1 : it;
+                stage_pos(kn, k, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1,
+                          (itn & 1) ? buf1 : buf0);
+                if (s + 2 < S) stage_ids((k + 2) % B, (s + 2) % 3);
+            }
+            const bool last_iter = (it + 1 == tk.iters);
+            bool need[RPT];
+#pragma unroll
+            for (int m = 0; m < RPT; m++)
+                need[m] = s > 0 && bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
+            if (tb == 0) trace_mark(tk, rank, s, 10);
+            add_tile(tile, kpn, need);
+            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * CR);
+            if (is_stager) cp_async_wait_all();   // staged data lands before "done"
+            if (tb == 0) trace_mark(tk, rank, s, 8);
+            bar_arrive_n(kBarDone, T);
+        }
+    }
 }
 
-template <int RPT, int T>
-__global__ void __launch_bounds__(T) exact_grid_kernel(ExactTask tk, ExactParams prm,
-                                                       float2* stage) {
-    GridBarrier bar{prm.bar, prm.status, gridDim.x, 0u};
-    exact_engine<RPT, T>(tk, prm, (int)blockIdx.x, (int)gridDim.x, bar, stage);
-}
-
-__global__ void energy_reduce_kernel(const double* __restrict__ epart, int iters, int B, int P,
+__global__ void energy_reduce_kernel(const double* __restrict__ e_iter, int iters, int G,
                                      double* __restrict__ energy) {
-    // one warp per iteration, fixed order: lanes stride over (batch, slot), then a
-    // butterfly of fixed shape
+    // one warp per iteration; fixed order over the per-CTA sums
     const int it = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (it >= iters) return;
-    const double* p = epart + (size_t)it * B * P;
+    const double* p = e_iter + (size_t)it * G;
     double e = 0.0;
-    for (int q = lane; q < B * P; q += 32) e += p[q];
+    for (int q = lane; q < G; q += 32) e += p[q];
     e = warp_sum_d(e);
     if (lane == 0) energy[it] = e;
 }
 
-bl_status energy_reduce(const double* epart, int iters, int B, int P, double* energy,
-                        cudaStream_t st) {
+bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, cudaStream_t st) {
     if (iters <= 0) return BL_OK;
     const int wpb = 8;
-    energy_reduce_kernel<<<div_up(iters, wpb), wpb * 32, 0, st>>>(epart, iters, B, P, energy);
+    energy_reduce_kernel<<<div_up(iters, wpb), wpb * 32, 0, st>>>(e_iter, iters, G, energy);
     BL_CUDA_TRY(cudaGetLastError());
     return BL_OK;
 }
@@ -293,73 +652,95 @@ bl_status energy_reduce(const double* epart, int iters, int B, int P, double* en
 // launcher
 // ---------------------------------------------------------------------------
 
-template <int RPT, int T>
-static bl_status launch_grid_t(const ExactTask& tk, const ExactParams& prm, cudaStream_t st,
-                               int G, float2* stage) {
-    auto kern = exact_grid_kernel<RPT, T>;
-    const size_t smem = (size_t)((tk.BS + 1) / 2) * sizeof(float4) +
-                        (size_t)tk.BS * sizeof(float4) + (T / 32) * sizeof(double);
+template <int RPT, int TB>
+static bl_status launch_grid_t(const ExactPlan& pl, const ExactTask& tk, const ExactParams& prm,
+                               cudaStream_t st) {
+    constexpr int T = TB + 32;
+    auto kern = exact_grid_kernel<RPT, TB>;
+    const EngineSmem L(tk.BS, div_up(tk.n, pl.G), tk.crit_cap, tk.nbr_cap, TB / 32);
+    const size_t smem = (size_t)L.total;
     BL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
     if (occ < 1) return set_error(BL_ECUDA, "exact engine: kernel does not fit on an SM");
-    const int max_g = occ * device_sm_count();
-    if (G > max_g) return set_error(BL_EINVAL, "exact engine: grid exceeds co-resident CTAs");
+    if (pl.G > occ * device_sm_count())
+        return set_error(BL_EINVAL, "exact engine: grid exceeds co-resident CTAs");
     ExactTask t = tk;
     ExactParams p = prm;
-    float2* s = stage;
-    void* args[] = {&t, &p, &s};
-    BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(T), args, smem, st));
+    void* args[] = {&t, &p};
+    BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(pl.G), dim3(T), args, smem, st));
     return BL_OK;
 }
-
-// rows-per-thread choices compiled in
-static const int kRptChoices[] = {1, 2, 3, 4, 6, 8};
-
-template <int T>
+template <int TB>
 static bl_status dispatch_rpt(const ExactPlan& pl, const ExactTask& tk, const ExactParams& prm,
-                              cudaStream_t st, float2* stage) {
+                              cudaStream_t st) {
     switch (pl.rpt) {
-        case 1: return launch_grid_t<1, T>(tk, prm, st, pl.G, stage);
-        case 2: return launch_grid_t<2, T>(tk, prm, st, pl.G, stage);
-        case 3: return launch_grid_t<3, T>(tk, prm, st, pl.G, stage);
-        case 4: return launch_grid_t<4, T>(tk, prm, st, pl.G, stage);
-        case 6: return launch_grid_t<6, T>(tk, prm, st, pl.G, stage);
-        case 8: return launch_grid_t<8, T>(tk, prm, st, pl.G, stage);
-        default: return set_error(BL_EINVAL, "exact engine: unsupported rows per thread");
+        case 1: return launch_grid_t<1, TB>(pl, tk, prm, st);
+        case 2: return launch_grid_t<2, TB>(pl, tk, prm, st);
+        case 3: return launch_grid_t<3, TB>(pl, tk, prm, st);
+        case 4: return launch_grid_t<4, TB>(pl, tk, prm, st);
+        default: break;
     }
+    if constexpr (TB == 256) {
+        switch (pl.rpt) {
+            case 6: return launch_grid_t<6, TB>(pl, tk, prm, st);
+            case 8: return launch_grid_t<8, TB>(pl, tk, prm, st);
+            default: break;
+        }
+    }
+    return set_error(BL_EINVAL, "exact engine: unsupported rows per thread");
 }
 
+// Launch shape: G = one CTA per SM (at least 64 rows each); bulk threads TB and
+// rows per thread by the rows per CTA: up to 512 rows one row per thread of 512,
+// up to 2048 rows 512 threads x 2..4 rows, beyond that 256 threads x 6..8 rows.
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out) {
     if (n <= 0 || BS <= 0) return set_error(BL_EINVAL, "exact engine: empty problem");
     const int sms = device_sm_count();
-    int T = threads_hint == 512 ? 512 : 256;
-    // default grid: one CTA per SM, but keep at least 64 rows per CTA
-    int G = ctas_hint > 0 ? ctas_hint : std::min(sms, std::max(1, div_up(n, 64)));
-    int rpt = div_up(div_up(n, G), T);
-    if (rpt > 8 && T == 256) {
-        T = 512;
-        rpt = div_up(div_up(n, G), T);
+    if (threads_hint <= 0) {   // tuning override: bulk threads per CTA
+        const char* e = std::getenv("BL_EXACT_THREADS");
+        if (e) threads_hint = std::atoi(e);
     }
+    const int G = ctas_hint > 0 ? ctas_hint : std::min(sms, std::max(1, div_up(n, 64)));
+    const int nloc = div_up(n, G);
+    int T = threads_hint == 256 || threads_hint == 512 ? threads_hint : (nloc <= 256 ? 256 : 512);
+    int rpt = div_up(nloc, T);
+    if (T == 512 && rpt > 4) {
+        T = 256;
+        rpt = div_up(nloc, T);
+    }
+    static const int kChoices256[] = {1, 2, 3, 4, 6, 8};
+    static const int kChoices512[] = {1, 2, 3, 4};
     int chosen = -1;
-    for (int c : kRptChoices)
-        if (c >= rpt) { chosen = c; break; }
-    if (chosen < 0) return set_error(BL_EINVAL, "exact engine: graph too large for the grid engine");
+    if (T == 256) {
+        for (int c : kChoices256)
+            if (c >= rpt) { chosen = c; break; }
+    } else {
+        for (int c : kChoices512)
+            if (c >= rpt) { chosen = c; break; }
+    }
+    if (chosen < 0)
+        return set_error(BL_EINVAL, "exact engine: too many vertices for exact mode (use BL_BH)");
     out->G = G;
     out->T = T;
     out->rpt = chosen;
-    const int rows_per = div_up(n, G);
-    out->P = div_up(BS, rows_per) + 1;
+    out->crit_cap = div_up(std::min(BS, n), G) + 1;
+    out->nbr_cap = 2048;
+    while (EngineSmem(BS, nloc, out->crit_cap, out->nbr_cap, T / 32).total > 200 * 1024 &&
+           out->nbr_cap > 256)
+        out->nbr_cap /= 2;
+    if (EngineSmem(BS, nloc, out->crit_cap, out->nbr_cap, T / 32).total > 220 * 1024)
+        return set_error(BL_EINVAL, "exact engine: batch too large for shared memory");
     return BL_OK;
 }
 
 bl_status exact_launch(const ExactPlan& pl, const ExactTask& task, const ExactParams& prm,
-                       float2* stage, cudaStream_t st) {
+                       cudaStream_t st) {
     if (task.n <= 0) return BL_OK;
     if (task.BS > kMaxBatch) return set_error(BL_EINVAL, "exact engine: batch too large");
     switch (pl.T) {
-        case 512: return dispatch_rpt<512>(pl, task, prm, st, stage);
-        default: return dispatch_rpt<256>(pl, task, prm, st, stage);
+        case 512: return dispatch_rpt<512>(pl, task, prm, st);
+        default: return dispatch_rpt<256>(pl, task, prm, st);
     }
 }
 

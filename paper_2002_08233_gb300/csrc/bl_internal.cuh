@@ -101,12 +101,16 @@ struct bl_layout {
     double last_ms = 0.0;
     bl::BHState* bh = nullptr;
     bl::Allocator alloc;
+    int trace_steps = 0;                // phase trace of the next run (0 = off)
+    bl::DevBuf trace;                   // uint64 timestamps
+    int64_t trace_count = 0;            // entries written by the last traced run
 };
 
 namespace bl {
 
 // device status word values are bl_status codes
 constexpr int kMaxBatch = 8192;
+constexpr int kTraceSlots = 12;   // timestamps per CTA and step in a phase trace
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 
 // ---------------------------------------------------------------------------
@@ -117,12 +121,16 @@ struct ExactTask {
     int n, BS, B;
     const int* rowptr;
     const int* colids;
-    float2* pos;
-    double* epart;       // [iters * B * P] energy partials, or null
+    float2* pos;         // positions at launch start (iteration parity 0 buffer)
+    float2* pos_alt;     // second position buffer (parity 1)
+    double* e_iter;      // [iters * G] per-CTA energies per iteration, or null
     float2* f_out;       // snapshot mode: forces of all n vertices
-    int P;               // energy slots per batch
     int iters;           // iterations in this launch (0 = snapshot mode)
     double step0;        // Step of the first iteration
+    int crit_cap;        // most rows of one batch a CTA owns
+    int nbr_cap;         // neighbour positions staged in shared memory
+    unsigned long long* trace;   // optional phase timestamps [G][trace_steps][kTraceSlots]
+    int trace_steps;
 };
 
 struct ExactParams {
@@ -130,24 +138,25 @@ struct ExactParams {
     float negRK2;        // -R K^2
     int repulse_neighbors;
     int* status;         // device status word
-    unsigned* bar;       // grid barrier counter
+    unsigned* bar;       // step counter (one arrival per CTA per step)
 };
 
 // Launch shape of the grid engine: G co-resident CTAs of T threads, rpt rows per
-// thread, P energy slots per batch (CTAs that can share one batch).
+// thread (row i lives on CTA i mod G).
 struct ExactPlan {
-    int G, T, rpt, P;
+    int G, T, rpt;
+    int crit_cap, nbr_cap;   // see ExactTask
 };
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out);
 
 // Runs task.iters iterations (or the one-snapshot forces when iters == 0) of one
-// graph on the grid engine; stage holds 2*BS float2. Returns after queuing.
+// graph on the grid engine. After an odd number of iterations the final
+// positions are in task.pos_alt. Returns after queuing.
 bl_status exact_launch(const ExactPlan& plan, const ExactTask& task, const ExactParams& prm,
-                       float2* stage, cudaStream_t st);
+                       cudaStream_t st);
 
-// Per-iteration energies from the partials: energy[t] = sum over batches and slots.
-bl_status energy_reduce(const double* epart, int iters, int B, int P, double* energy,
-                        cudaStream_t st);
+// Per-iteration energies: energy[t] = sum over CTAs of e_iter[t][cta], in order.
+bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // helpers

@@ -141,15 +141,17 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     const int n = L->g->n;
     ExactPlan plan;
     BL_TRY(exact_plan(n, BS, 0, 0, &plan));
-    const int B = div_up(n, BS);
     ExactTask tk{};
     tk.n = n;
     tk.BS = BS;
-    tk.B = B;
+    tk.B = div_up(n, BS);
     tk.rowptr = L->g->rowptr.as<int>();
     tk.colids = L->g->colids.as<int>();
+    BL_TRY(L->pos2.ensure(L->alloc, (size_t)n * sizeof(float2)));
     tk.pos = L->pos.as<float2>();
-    tk.P = plan.P;
+    tk.pos_alt = L->pos2.as<float2>();
+    tk.crit_cap = plan.crit_cap;
+    tk.nbr_cap = plan.nbr_cap;
     tk.iters = snapshot ? 0 : iters;
     {   // Step_t by repeated multiplication, as Algorithm 2 schedules it
         double s = 1.0;
@@ -157,14 +159,18 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
         tk.step0 = s;
     }
     tk.f_out = f_out;
-    const size_t stage_bytes = (size_t)2 * BS * sizeof(float2);
-    if (!snapshot) {
-        const size_t ep = (size_t)iters * B * plan.P * sizeof(double);
-        BL_TRY(L->epart.ensure(L->alloc, ep));
-        BL_CUDA_TRY(cudaMemsetAsync(L->epart.p, 0, ep, st));
-        tk.epart = L->epart.as<double>();
+    if (!snapshot && L->trace_steps > 0) {
+        const size_t tb = (size_t)plan.G * L->trace_steps * kTraceSlots * sizeof(unsigned long long);
+        BL_TRY(L->trace.ensure(L->alloc, tb));
+        BL_CUDA_TRY(cudaMemsetAsync(L->trace.p, 0, tb, st));
+        tk.trace = L->trace.as<unsigned long long>();
+        tk.trace_steps = L->trace_steps;
+        L->trace_count = (int64_t)plan.G * L->trace_steps * kTraceSlots;
     }
-    BL_TRY(L->pos2.ensure(L->alloc, std::max(stage_bytes, (size_t)n * sizeof(float2))));
+    if (!snapshot) {
+        BL_TRY(L->epart.ensure(L->alloc, (size_t)iters * plan.G * sizeof(double)));
+        tk.e_iter = L->epart.as<double>();
+    }
     ExactParams prm{};
     prm.invK = 1.0f / L->prm.K;
     prm.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
@@ -172,10 +178,11 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     prm.status = static_cast<int*>(L->status.p);
     prm.bar = layout_barrier_word(L);
     BL_TRY(layout_reset_sync_words(L, st));
-    BL_TRY(exact_launch(plan, tk, prm, L->pos2.as<float2>(), st));
+    BL_TRY(exact_launch(plan, tk, prm, st));
     if (!snapshot) {
         BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(iters, 1) * sizeof(double)));
-        BL_TRY(energy_reduce(L->epart.as<double>(), iters, B, plan.P, L->energy.as<double>(), st));
+        BL_TRY(energy_reduce(L->epart.as<double>(), iters, plan.G, L->energy.as<double>(), st));
+        if (iters & 1) std::swap(L->pos, L->pos2);   // final positions are in the other buffer
     }
     return BL_OK;
 }
@@ -446,6 +453,7 @@ void bl_layout_free(bl_layout* L) {
     L->epart.release();
     L->status.release();
     L->scratch.release();
+    L->trace.release();
     delete L;
 }
 
@@ -474,6 +482,24 @@ bl_status bl_debug_forces(bl_layout* L, bl_mode mode, float theta, int32_t lo, i
     BL_CUDA_TRY(cudaMemcpyAsync(f_out, f + lo, (size_t)(hi - lo) * sizeof(float2), cudaMemcpyDeviceToHost, st));
     BL_CUDA_TRY(cudaStreamSynchronize(st));
     return check_stream_status(L);
+}
+
+bl_status bl_set_trace(bl_layout* L, int32_t max_steps) {
+    if (!L || max_steps < 0) return set_error(BL_EINVAL, "bl_set_trace: bad argument");
+    L->trace_steps = max_steps;
+    return BL_OK;
+}
+
+bl_status bl_get_trace(const bl_layout* L, uint64_t* out, int64_t cap, int64_t* count) {
+    if (!L || !count) return set_error(BL_EINVAL, "bl_get_trace: NULL argument");
+    *count = L->trace_count;
+    if (!out || L->trace_count == 0) return BL_OK;
+    if (cap < L->trace_count) return set_error(BL_EINVAL, "bl_get_trace: output too small");
+    cudaStream_t st = current_stream();
+    BL_CUDA_TRY(cudaMemcpyAsync(out, L->trace.p, (size_t)L->trace_count * sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, st));
+    BL_CUDA_TRY(cudaStreamSynchronize(st));
+    return BL_OK;
 }
 
 bl_status bl_debug_bh_tree(bl_layout* L, uint32_t* codes, int32_t* perm, int32_t* first,
