@@ -86,8 +86,9 @@ typedef struct {
     double energy;               /* sum |ct_i|^2 of the last iteration (FP64) */
     double pair_interactions;    /* exact mode: n(n-1) per iteration, cumulative */
     double vertex_updates;       /* n per iteration, cumulative */
-    double bh_far_nodes;         /* BH: accepted far-field nodes, last iteration */
-    double bh_near_pairs;        /* BH: directly summed leaf pairs, last iteration */
+    double bh_far_nodes;         /* BH: accepted far-field nodes, last tree walk */
+    double bh_near_pairs;        /* BH: leaf vertices visited (each query's own
+                                    vertex included), last tree walk */
     double last_run_ms;          /* device time of the last bl_layout_run */
 } bl_stats_t;
 

@@ -1,18 +1,930 @@
-// Barnes-Hut engine (Section 3.5, Algorithms S3-S5). Placeholder until the
-// Morton sort, tree build and walk kernels land.
+// Barnes-Hut BatchLayout (Section 3.5; Algorithms S3, S4, S5).
+//
+// One iteration, on the snapshot S of the positions at iteration start
+// (Algorithm S5 builds the tree before its minibatch loop):
+//   1. bounding box -> root square (side D = max extent, anchored at the minimum);
+//   2. Morton codes: each coordinate quantised to 16 bits in FP32 with a fixed op
+//      order, bits interleaved (x in even bits, y in odd bits);
+//   3. stable LSD radix sort of (code, vertex id), 4 passes of 8 bits;
+//   4. quadtree in pre-order, built bottom-up from the sorted codes: a node is a
+//      non-empty cell whose parent holds >= 2 vertices; it is a leaf when it holds
+//      one vertex or sits at level 16. Sorted position k starts the cells of the
+//      levels between the first level where its code differs from code[k-1] and
+//      the first level where it differs from code[k+1]; an exclusive scan of those
+//      counts gives every node its pre-order index, and a binary search gives each
+//      cell's end and the index just past its subtree (skip);
+//   5. node coordinate sums in FP32, level by level from the leaves: a leaf adds
+//      its vertices in sorted order, an inner node adds its children in order;
+//      centroid = sum / count;
+//   6. theta-walk per vertex (S4): stackless pre-order traversal with skip links; a
+//      node is accepted when (D/2^level)^2 < theta^2 * |g - c_i|^2 (FP32) and then
+//      acts with its vertex count at its centroid; leaves add their vertices
+//      directly (vertex i itself skipped by index). The 32 lanes of a warp walk 32
+//      Morton-adjacent vertices and advance together to the smallest node any of
+//      them still has to visit, so each node record is read once per warp;
+//   7. neighbour correction: unless repulse_neighbors, the exact repulsion of each
+//      vertex's CSR neighbours (at S) is taken back out;
+//   8. minibatch sweep: batches in vertex-id order; the rows of batch b add the CSR
+//      attraction at the live positions (earlier batches already moved this
+//      iteration) to their repulsion and move by Step * ct/|ct|. Batch b depends
+//      only on the earlier batches its rows have edges into: a persistent kernel
+//      processes batches as their predecessors' flags appear.
+// Positions are double-buffered: the sweep reads S (not yet moved vertices) from
+// the old buffer and writes the new buffer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "bl_internal.cuh"
 
 namespace bl {
-struct BHState {};
-void bh_state_free(BHState* s) { delete s; }
-bl_status bh_run(bl_layout*, int, int, float, cudaStream_t) {
-    return set_error(BL_EINVAL, "Barnes-Hut mode is not built yet");
+
+constexpr int kLevels = 16;
+constexpr int kScanItems = 1024;     // elements per block of the scan
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;       // elements per thread of a sort tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSweepThreads = 256;
+
+struct BHState {
+    int n = 0;
+    int64_t cap_nodes = 0;
+    DevBuf keys0, keys1, vals0, vals1;   // sort ping-pong
+    DevBuf hist, scan_part;             // radix digit counts, scan block sums
+    DevBuf bpart, box;                  // bbox partials; box = {xmin, ymin, D, s, Dl2[17]}
+    DevBuf cnt;                         // int[n+1]: nodes per sorted position -> first node
+    DevBuf spos;                        // float2[n]: positions in sorted order
+    DevBuf nd_first, nd_count, nd_level, nd_skip;
+    DevBuf nd_sum;                      // float2 sums
+    DevBuf nd_rec;                      // float4 {gx, gy, Dl^2, count}
+    DevBuf nd_aux;                      // int2 {skip, leaf ? first : -1}
+    DevBuf lvl;                         // int[64]: per-level counts, offsets, fill
+    DevBuf lvl_nodes;                   // nodes bucketed by level
+    DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
+    DevBuf walkcnt;                     // unsigned long long[2]: far nodes, near pairs
+    // sweep
+    int preds_bs = -1, B = 0;
+    DevBuf flags;                       // int[B]: iteration stamp of the last update
+    DevBuf preds_ptr, preds;            // predecessor batches, most recent first
+    DevBuf epart;                       // double[B] energy per batch
+    int stamp = 0;
+};
+
+void bh_state_free(BHState* s) {
+    if (!s) return;
+    DevBuf* bufs[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->hist, &s->scan_part,
+                      &s->bpart, &s->box, &s->cnt, &s->spos, &s->nd_first, &s->nd_count,
+                      &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
+                      &s->lvl_nodes, &s->rep, &s->walkcnt, &s->flags, &s->preds_ptr, &s->preds,
+                      &s->epart};
+    for (DevBuf* b : bufs) b->release();
+    delete s;
 }
-bl_status bh_debug_forces(bl_layout*, float, float2*, cudaStream_t) {
-    return set_error(BL_EINVAL, "Barnes-Hut mode is not built yet");
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (device-wide, three kernels)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int block_exclusive_scan_256(int v, int* s_warp, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < 8 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < 8) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[7];
+    const int before = warp > 0 ? s_warp[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
 }
-bl_status bh_debug_tree(bl_layout*, uint32_t*, int32_t*, int32_t*, int32_t*, int32_t*, int32_t*,
-                        float*, float*, int64_t, int64_t*, float*, cudaStream_t) {
-    return set_error(BL_EINVAL, "Barnes-Hut mode is not built yet");
+
+__global__ void scan_sums_kernel(const int* __restrict__ in, int n, int* __restrict__ part) {
+    __shared__ int s_warp[8];
+    const int base = blockIdx.x * kScanItems;
+    int v = 0;
+    for (int q = 0; q < 4; q++) {
+        const int idx = base + threadIdx.x * 4 + q;
+        v += idx < n ? in[idx] : 0;
+    }
+    int total;
+    block_exclusive_scan_256(v, s_warp, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
+
+__global__ void scan_top_kernel(int* __restrict__ part, int nb) {
+    // single block of 256 threads: exclusive scan over nb block sums, in place
+    __shared__ int s_warp[8];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 256) {
+        const int idx = base + threadIdx.x;
+        const int v = idx < nb ? part[idx] : 0;
+        int total;
+        const int ex = block_exclusive_scan_256(v, s_warp, total);
+        if (idx < nb) part[idx] = s_carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_apply_kernel(const int* in, int n, const int* __restrict__ part, int* out) {
+    __shared__ int s_warp[8];
+    const int base = blockIdx.x * kScanItems;
+    int v[4];
+    int sum = 0;
+    for (int q = 0; q < 4; q++) {
+        const int idx = base + threadIdx.x * 4 + q;
+        v[q] = idx < n ? in[idx] : 0;
+        sum += v[q];
+    }
+    int total;
+    int run = block_exclusive_scan_256(sum, s_warp, total) + part[blockIdx.x];
+    for (int q = 0; q < 4; q++) {
+        const int idx = base + threadIdx.x * 4 + q;
+        if (idx < n) out[idx] = run;
+        run += v[q];
+    }
+}
+
+// exclusive scan in -> out (may alias); part holds ceil(n/1024) ints
+static bl_status exclusive_scan(const int* in, int* out, int n, int* part, cudaStream_t st) {
+    const int nb = div_up(n, kScanItems);
+    scan_sums_kernel<<<nb, 256, 0, st>>>(in, n, part);
+    scan_top_kernel<<<1, 256, 0, st>>>(part, nb);
+    scan_apply_kernel<<<nb, 256, 0, st>>>(in, n, part, out);
+    BL_CUDA_TRY(cudaGetLastError());
+    return BL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// bounding box and Morton codes (reading R8, R9)
+// ---------------------------------------------------------------------------
+
+__global__ void bbox_partial_kernel(const float2* __restrict__ pos, int n, float4* __restrict__ part) {
+    float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 p = pos[i];
+        xmin = fminf(xmin, p.x);
+        xmax = fmaxf(xmax, p.x);
+        ymin = fminf(ymin, p.y);
+        ymax = fmaxf(ymax, p.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    }
+    __shared__ float4 s_w[32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = make_float4(xmin, xmax, ymin, ymax);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 r = s_w[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            r.x = fminf(r.x, s_w[w].x);
+            r.y = fmaxf(r.y, s_w[w].y);
+            r.z = fminf(r.z, s_w[w].z);
+            r.w = fmaxf(r.w, s_w[w].w);
+        }
+        part[blockIdx.x] = r;
+    }
+}
+
+// box[0] = xmin, box[1] = ymin, box[2] = D, box[3] = 65536/D (0 when the box is
+// degenerate: every code is then 0), box[4 + l] = (D * 2^-l)^2 for l = 0..16
+__global__ void bbox_final_kernel(const float4* __restrict__ part, int nb, float* __restrict__ box) {
+    if (threadIdx.x != 0) return;
+    float4 r = part[0];
+    for (int b = 1; b < nb; b++) {
+        r.x = fminf(r.x, part[b].x);
+        r.y = fmaxf(r.y, part[b].y);
+        r.z = fminf(r.z, part[b].z);
+        r.w = fmaxf(r.w, part[b].w);
+    }
+    const float dxr = __fsub_rn(r.y, r.x), dyr = __fsub_rn(r.w, r.z);
+    const float D = dxr > dyr ? dxr : dyr;
+    box[0] = r.x;
+    box[1] = r.z;
+    box[2] = D;
+    box[3] = (D > 0.f && isfinite(D)) ? __fdiv_rn(65536.0f, D) : 0.f;
+    for (int l = 0; l <= kLevels; l++) {
+        const float Dl = ldexpf(D, -l);
+        box[4 + l] = __fmul_rn(Dl, Dl);
+    }
+}
+
+// spread the 16 bits of v to the even bit positions
+__device__ __forceinline__ unsigned spread_bits(unsigned v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__global__ void morton_kernel(const float2* __restrict__ pos, int n, const float* __restrict__ box,
+                              unsigned* __restrict__ keys, int* __restrict__ vals) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float s = box[3];
+    unsigned code = 0u;
+    if (s > 0.f) {
+        const float2 p = pos[i];
+        const float tx = __fmul_rn(__fsub_rn(p.x, box[0]), s);
+        const float ty = __fmul_rn(__fsub_rn(p.y, box[1]), s);
+        unsigned qx = (unsigned)floorf(tx), qy = (unsigned)floorf(ty);
+        qx = min(qx, 65535u);
+        qy = min(qy, 65535u);
+        code = spread_bits(qx) | (spread_bits(qy) << 1);
+    }
+    keys[i] = code;
+    vals[i] = i;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (u32 key, i32 value), 8 bits per pass
+// ---------------------------------------------------------------------------
+
+__global__ void radix_hist_kernel(const unsigned* __restrict__ keys, int n, int shift, int nblocks,
+                                  int* __restrict__ hist) {
+    __shared__ int s_cnt[256];
+    s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile;
+    for (int q = 0; q < kSortItems; q++) {
+        const int idx = base + q * kSortThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&s_cnt[(keys[idx] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = s_cnt[threadIdx.x];   // digit-major
+}
+
+__global__ void radix_scatter_kernel(const unsigned* __restrict__ kin, const int* __restrict__ vin,
+                                     int n, int shift, int nblocks, const int* __restrict__ offs,
+                                     unsigned* __restrict__ kout, int* __restrict__ vout) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ int s_run[256];
+    __shared__ int s_wcnt[W][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    s_run[threadIdx.x] = offs[threadIdx.x * nblocks + blockIdx.x];
+    for (int w = 0; w < W; w++) s_wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const int base = blockIdx.x * kSortTile;
+    for (int q = 0; q < kSortItems; q++) {   // chunks in index order: stable
+        const int idx = base + q * kSortThreads + threadIdx.x;
+        const bool valid = idx < n;
+        const unsigned key = valid ? kin[idx] : 0u;
+        const int d = valid ? (int)((key >> shift) & 255u) : 256;   // 256: no digit
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) s_wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int before = 0;
+            for (int w = 0; w < warp; w++) before += s_wcnt[w][d];
+            const int dst = s_run[d] + before + rank;
+            kout[dst] = key;
+            vout[dst] = vin[idx];
+        }
+        __syncthreads();
+        int tot = 0;
+        for (int w = 0; w < W; w++) {
+            tot += s_wcnt[w][threadIdx.x];
+            s_wcnt[w][threadIdx.x] = 0;
+        }
+        s_run[threadIdx.x] += tot;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// quadtree (reading R10) and node sums (R11)
+// ---------------------------------------------------------------------------
+
+// levels 0..L share their prefix when the codes agree on the top 2L bits
+__device__ __forceinline__ int common_levels(unsigned a, unsigned b) {
+    const unsigned x = a ^ b;
+    return x == 0u ? kLevels : (__clz(x) >> 1);
+}
+
+__device__ __forceinline__ void node_levels(const unsigned* codes, int n, int k, int& lmin,
+                                            int& lmax) {
+    const unsigned c = codes[k];
+    if (k > 0 && codes[k - 1] == c) {   // no cell starts here
+        lmin = 1;
+        lmax = 0;
+        return;
+    }
+    lmin = k == 0 ? 0 : common_levels(codes[k - 1], c) + 1;
+    if (k == n - 1) {
+        lmax = lmin;
+    } else {
+        lmax = min(kLevels, max(lmin, common_levels(c, codes[k + 1]) + 1));
+    }
+}
+
+__global__ void node_count_kernel(const unsigned* __restrict__ codes, int n, int* __restrict__ cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n) return;
+    if (k == n) {
+        cnt[n] = 0;
+        return;
+    }
+    int lmin, lmax;
+    node_levels(codes, n, k, lmin, lmax);
+    cnt[k] = lmax - lmin + 1;
+}
+
+// first index >= lo whose top 2l bits differ from `prefix` (codes sorted)
+__device__ __forceinline__ int cell_end(const unsigned* codes, int n, int lo, unsigned c, int l) {
+    if (l == 0) return n;
+    const unsigned mask = l >= kLevels ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2 * l));
+    const unsigned top = c & mask;
+    int a = lo, b = n;   // codes[a] has the prefix; find the first > top|~mask
+    const unsigned last = top | ~mask;
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        if (codes[m] <= last)
+            a = m + 1;
+        else
+            b = m;
+    }
+    return a;
+}
+
+__global__ void node_emit_kernel(const unsigned* __restrict__ codes, int n,
+                                 const int* __restrict__ first_node, int* __restrict__ nd_first,
+                                 int* __restrict__ nd_count, int* __restrict__ nd_level,
+                                 int* __restrict__ nd_skip, int* __restrict__ lvl_cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int lmin, lmax;
+    node_levels(codes, n, k, lmin, lmax);
+    if (lmax < lmin) return;
+    const int M = first_node[n];
+    const unsigned c = codes[k];
+    int v = first_node[k];
+    for (int l = lmin; l <= lmax; l++, v++) {
+        const int e = cell_end(codes, n, k + 1, c, l);
+        nd_first[v] = k;
+        nd_count[v] = e - k;
+        nd_level[v] = l;
+        nd_skip[v] = e >= n ? M : first_node[e];
+        atomicAdd(&lvl_cnt[l], 1);
+    }
+}
+
+// lvl[0..16] counts -> lvl[20..37] offsets, lvl[40..56] fill cursors
+__global__ void level_offsets_kernel(int* __restrict__ lvl) {
+    if (threadIdx.x != 0) return;
+    int acc = 0;
+    for (int l = 0; l <= kLevels; l++) {
+        lvl[20 + l] = acc;
+        lvl[40 + l] = acc;
+        acc += lvl[l];
+    }
+    lvl[20 + kLevels + 1] = acc;
+}
+
+__global__ void level_bucket_kernel(const int* __restrict__ nd_level, const int* __restrict__ first_node,
+                                    int n, int* __restrict__ lvl, int* __restrict__ lvl_nodes) {
+    const int M = first_node[n];
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M; v += gridDim.x * blockDim.x) {
+        const int slot = atomicAdd(&lvl[40 + nd_level[v]], 1);
+        lvl_nodes[slot] = v;
+    }
+}
+
+__global__ void level_sums_kernel(int l, const int* __restrict__ lvl, const int* __restrict__ lvl_nodes,
+                                  const float2* __restrict__ spos, const int* __restrict__ nd_first,
+                                  const int* __restrict__ nd_count, const int* __restrict__ nd_skip,
+                                  const float* __restrict__ box, float2* __restrict__ nd_sum,
+                                  float4* __restrict__ nd_rec, int2* __restrict__ nd_aux) {
+    const int lo = lvl[20 + l], hi = lvl[20 + l + 1];
+    const float Dl2 = box[4 + l];
+    for (int q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) {
+        const int v = lvl_nodes[q];
+        const int cnt = nd_count[v];
+        const int skip = nd_skip[v];
+        const bool leaf = cnt == 1 || l == kLevels;
+        float sx, sy;
+        if (leaf) {
+            const int f = nd_first[v];
+            sx = 0.f;
+            sy = 0.f;
+            for (int m = 0; m < cnt; m++) {   // vertices in sorted order
+                const float2 p = spos[f + m];
+                sx = __fadd_rn(sx, p.x);
+                sy = __fadd_rn(sy, p.y);
+            }
+        } else {
+            int c = v + 1;   // children in order, via skip links
+            sx = nd_sum[c].x;
+            sy = nd_sum[c].y;
+            c = nd_skip[c];
+            while (c < skip) {
+                sx = __fadd_rn(sx, nd_sum[c].x);
+                sy = __fadd_rn(sy, nd_sum[c].y);
+                c = nd_skip[c];
+            }
+        }
+        nd_sum[v] = make_float2(sx, sy);
+        const float fc = (float)cnt;
+        nd_rec[v] = make_float4(__fdiv_rn(sx, fc), __fdiv_rn(sy, fc), Dl2, fc);
+        nd_aux[v] = make_int2(skip, leaf ? nd_first[v] : -1);
+    }
+}
+
+__global__ void gather_sorted_kernel(const int* __restrict__ perm, const float2* __restrict__ pos,
+                                     int n, float2* __restrict__ spos) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) spos[k] = pos[perm[k]];
+}
+
+// ---------------------------------------------------------------------------
+// theta-walk (Algorithm S4), warp-cooperative, Kahan-compensated
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) walk_kernel(
+    const int* __restrict__ perm, const float2* __restrict__ spos, const int* __restrict__ first_node,
+    int n, const float4* __restrict__ nd_rec, const int2* __restrict__ nd_aux, float theta2,
+    float2* __restrict__ rep, unsigned long long* __restrict__ counts) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;   // sorted position = query
+    const int M = first_node[n];
+    const bool active = q < n;
+    const int i = active ? perm[q] : -1;
+    const float2 me = active ? spos[q] : make_float2(0.f, 0.f);
+    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+    unsigned next = active ? 0u : (unsigned)M;
+    unsigned far = 0, near = 0;
+    auto visit = [&](unsigned v) {
+        const float4 rec = nd_rec[v];
+        const int2 aux = nd_aux[v];
+        if (aux.y >= 0) {   // leaf: its vertices directly, self skipped by index
+            const int cnt = (int)rec.w;
+            near += (unsigned)cnt;   // leaf vertices visited, the query's own included
+            for (int m = 0; m < cnt; m++) {
+                const int k = aux.y + m;
+                if (perm[k] == i) continue;
+                const float2 p = cnt == 1 ? make_float2(rec.x, rec.y) : spos[k];
+                float ax = 0.f, ay = 0.f;
+                rep_pair(me.x, me.y, p.x, p.y, ax, ay);
+                kahan_add(sx, cx, ax);
+                kahan_add(sy, cy, ay);
+            }
+            next = v + 1u;
+        } else {
+            const float dx = __fsub_rn(rec.x, me.x);
+            const float dy = __fsub_rn(rec.y, me.y);
+            const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+            if (rec.z < __fmul_rn(theta2, d2)) {   // acceptance test (Section 3.5)
+                const float w = __fmul_rn(rec.w, rcp_sfu(d2));
+                kahan_add(sx, cx, dx * w);
+                kahan_add(sy, cy, dy * w);
+                far++;
+                next = (unsigned)aux.x;
+            } else {
+                next = v + 1u;
+            }
+        }
+    };
+    for (;;) {
+        const unsigned v = __reduce_min_sync(0xffffffffu, next);
+        if (v >= (unsigned)M) break;
+        if (next == v) visit(v);
+    }
+    if (active) rep[i] = make_float2(sx - cx, sy - cy);
+    // interaction counts for reporting
+    unsigned long long f = far, nr = near;
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+        nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    }
+    if ((threadIdx.x & 31) == 0 && counts != nullptr) {
+        atomicAdd(&counts[0], f);
+        atomicAdd(&counts[1], nr);
+    }
+}
+
+// rep[i] -= exact repulsion of i's CSR neighbours at S (warp per row)
+__global__ void nbr_correct_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
+                                   const float2* __restrict__ S, int n, float2* __restrict__ rep) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int i = warp;
+    const float2 me = S[i];
+    float ax = 0.f, ay = 0.f;
+    for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+        const float2 p = S[colids[e]];
+        rep_pair(me.x, me.y, p.x, p.y, ax, ay);
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) {
+        const float2 r = rep[i];
+        rep[i] = make_float2(r.x - ax, r.y - ay);
+    }
+}
+
+// snapshot forces: ct_i = attraction at S + (-R K^2) rep_i (warp per row)
+__global__ void bh_snapshot_force_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
+                                         const float2* __restrict__ S, int n, const float2* __restrict__ rep,
+                                         float invK, float negRK2, float2* __restrict__ out) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int i = warp;
+    const float2 me = S[i];
+    float ax = 0.f, ay = 0.f;
+    for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+        const float2 p = S[colids[e]];
+        const float dx = p.x - me.x, dy = p.y - me.y;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
+        const float a = d2 * rsqrt_sfu(d2) * invK;
+        ax = fmaf(dx, a, ax);
+        ay = fmaf(dy, a, ay);
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) {
+        const float2 r = rep[i];
+        out[i] = make_float2(fmaf(negRK2, r.x, ax), fmaf(negRK2, r.y, ay));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// minibatch sweep (Algorithm S5's batch loop)
+// ---------------------------------------------------------------------------
+
+struct SweepArgs {
+    const int* rowptr;
+    const int* colids;
+    const float2* bold;      // positions at iteration start (S)
+    float2* bnew;            // positions after this iteration's update
+    const float2* rep;       // repulsion sums (unscaled)
+    int* flags;
+    const int* preds_ptr;
+    const int* preds;
+    double* epart;
+    int* status;
+    int n, BS, B, stamp;
+    float invK, negRK2, stepf;
+};
+
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
+    constexpr int W = kSweepThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double s_e[W];
+    __shared__ int s_ok;
+    for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
+        // wait for every earlier batch this batch's rows have edges into (bounded)
+        if (warp == 0) {
+            int ok = 1;
+            const unsigned long long t0 = global_ns();
+            for (int p = a.preds_ptr[b] + lane; p < a.preds_ptr[b + 1]; p += 32) {
+                const int* f = a.flags + a.preds[p];
+                unsigned spin = 0;
+                while (ok) {
+                    if (ld_volatile_i32(f) >= a.stamp) break;
+                    if ((++spin & 255u) == 0u) {
+                        if (ld_volatile_i32(a.status) != 0) ok = 0;
+                        else if (global_ns() - t0 > kWaitLimitNs) {
+                            atomicCAS(a.status, 0, (int)BL_ETIMEOUT);
+                            ok = 0;
+                        }
+                    }
+                }
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            __threadfence();   // acquire side: the flags seen above order the loads below
+            if (lane == 0) s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int lo = b * a.BS, hi = min(a.n, lo + a.BS);
+        double e_acc = 0.0;
+        for (int i = lo + warp; i < hi; i += W) {
+            const float2 me = a.bold[i];
+            float ax = 0.f, ay = 0.f;
+            const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const int j = a.colids[e];
+                const float2 p = j < lo ? __ldcg(&a.bnew[j]) : a.bold[j];
+                const float dx = p.x - me.x, dy = p.y - me.y;
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
+                const float s = d2 * rsqrt_sfu(d2) * a.invK;
+                ax = fmaf(dx, s, ax);
+                ay = fmaf(dy, s, ay);
+            }
+            ax = warp_sum(ax);
+            ay = warp_sum(ay);
+            if (lane == 0) {
+                const float2 r = a.rep[i];
+                const float fx = fmaf(a.negRK2, r.x, ax);
+                const float fy = fmaf(a.negRK2, r.y, ay);
+                float nx = me.x, ny = me.y, gx = fx, gy = fy;
+                float n2 = fmaf(gx, gx, gy * gy);
+                if (n2 > 0.f) {
+                    if (!(n2 < INFINITY)) {
+                        gx *= 0x1p-64f;
+                        gy *= 0x1p-64f;
+                        n2 = fmaf(gx, gx, gy * gy);
+                    }
+                    const float sc = a.stepf * rsqrt_sfu(n2);
+                    nx = fmaf(sc, gx, me.x);
+                    ny = fmaf(sc, gy, me.y);
+                }
+                a.bnew[i] = make_float2(nx, ny);
+                e_acc += (double)fmaf(fx, fx, fy * fy);
+            }
+        }
+        if (lane == 0) s_e[warp] = e_acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double e = 0.0;
+            for (int w = 0; w < W; w++) e += s_e[w];
+            a.epart[b] = e;
+            __threadfence();
+            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a.flags + b), "r"(a.stamp)
+                         : "memory");
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void batch_energy_kernel(const double* __restrict__ epart, int B, double* __restrict__ out) {
+    // one warp, fixed order
+    double e = 0.0;
+    for (int b = threadIdx.x; b < B; b += 32) e += epart[b];
+    e = warp_sum_d(e);
+    if (threadIdx.x == 0) *out = e;
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+
+static bl_status bh_ensure(bl_layout* L) {
+    const int n = L->g->n;
+    if (!L->bh) L->bh = new BHState();
+    BHState* s = L->bh;
+    if (s->n == n && s->cap_nodes > 0) return BL_OK;
+    const Allocator& al = L->alloc;
+    const size_t N = (size_t)n;
+    const int nb_sort = div_up(n, kSortTile);
+    const int64_t cap = 17 * (int64_t)n + 1;
+    BL_TRY(s->keys0.ensure(al, N * 4));
+    BL_TRY(s->keys1.ensure(al, N * 4));
+    BL_TRY(s->vals0.ensure(al, N * 4));
+    BL_TRY(s->vals1.ensure(al, N * 4));
+    BL_TRY(s->hist.ensure(al, (size_t)256 * nb_sort * 4));
+    BL_TRY(s->scan_part.ensure(al, (size_t)(div_up(std::max<int64_t>(cap, (int64_t)256 * nb_sort), kScanItems) + 1) * 4));
+    BL_TRY(s->bpart.ensure(al, 1024 * sizeof(float4)));
+    BL_TRY(s->box.ensure(al, 32 * sizeof(float)));
+    BL_TRY(s->cnt.ensure(al, (N + 1) * 4));
+    BL_TRY(s->spos.ensure(al, N * sizeof(float2)));
+    BL_TRY(s->nd_first.ensure(al, (size_t)cap * 4));
+    BL_TRY(s->nd_count.ensure(al, (size_t)cap * 4));
+    BL_TRY(s->nd_level.ensure(al, (size_t)cap * 4));
+    BL_TRY(s->nd_skip.ensure(al, (size_t)cap * 4));
+    BL_TRY(s->nd_sum.ensure(al, (size_t)cap * sizeof(float2)));
+    BL_TRY(s->nd_rec.ensure(al, (size_t)cap * sizeof(float4)));
+    BL_TRY(s->nd_aux.ensure(al, (size_t)cap * sizeof(int2)));
+    BL_TRY(s->lvl.ensure(al, 64 * 4));
+    BL_TRY(s->lvl_nodes.ensure(al, (size_t)cap * 4));
+    BL_TRY(s->rep.ensure(al, N * sizeof(float2)));
+    BL_TRY(s->walkcnt.ensure(al, 2 * sizeof(unsigned long long)));
+    s->n = n;
+    s->cap_nodes = cap;
+    return BL_OK;
+}
+
+// Builds the tree of positions S; leaves codes/perm (sorted) in keys0/vals0.
+static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st) {
+    BHState* s = L->bh;
+    const int n = L->g->n;
+    const int nbb = std::min(1024, div_up(n, 256));
+    bbox_partial_kernel<<<nbb, 256, 0, st>>>(S, n, s->bpart.as<float4>());
+    bbox_final_kernel<<<1, 32, 0, st>>>(s->bpart.as<float4>(), nbb, s->box.as<float>());
+    morton_kernel<<<div_up(n, 256), 256, 0, st>>>(S, n, s->box.as<float>(), s->keys0.as<unsigned>(),
+                                                  s->vals0.as<int>());
+    const int nbs = div_up(n, kSortTile);
+    unsigned* kin = s->keys0.as<unsigned>();
+    unsigned* kout = s->keys1.as<unsigned>();
+    int* vin = s->vals0.as<int>();
+    int* vout = s->vals1.as<int>();
+    for (int pass = 0; pass < 4; pass++) {
+        const int shift = 8 * pass;
+        radix_hist_kernel<<<nbs, kSortThreads, 0, st>>>(kin, n, shift, nbs, s->hist.as<int>());
+        BL_TRY(exclusive_scan(s->hist.as<int>(), s->hist.as<int>(), 256 * nbs, s->scan_part.as<int>(), st));
+        radix_scatter_kernel<<<nbs, kSortThreads, 0, st>>>(kin, vin, n, shift, nbs, s->hist.as<int>(),
+                                                            kout, vout);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    // after 4 passes the sorted data is back in keys0/vals0
+    gather_sorted_kernel<<<div_up(n, 256), 256, 0, st>>>(vin, S, n, s->spos.as<float2>());
+    node_count_kernel<<<div_up(n + 1, 256), 256, 0, st>>>(kin, n, s->cnt.as<int>());
+    BL_TRY(exclusive_scan(s->cnt.as<int>(), s->cnt.as<int>(), n + 1, s->scan_part.as<int>(), st));
+    BL_CUDA_TRY(cudaMemsetAsync(s->lvl.p, 0, 64 * 4, st));
+    node_emit_kernel<<<div_up(n, 256), 256, 0, st>>>(kin, n, s->cnt.as<int>(), s->nd_first.as<int>(),
+                                                     s->nd_count.as<int>(), s->nd_level.as<int>(),
+                                                     s->nd_skip.as<int>(), s->lvl.as<int>());
+    level_offsets_kernel<<<1, 32, 0, st>>>(s->lvl.as<int>());
+    const int sms = device_sm_count();
+    level_bucket_kernel<<<sms * 4, 256, 0, st>>>(s->nd_level.as<int>(), s->cnt.as<int>(), n,
+                                                 s->lvl.as<int>(), s->lvl_nodes.as<int>());
+    for (int l = kLevels; l >= 0; l--)
+        level_sums_kernel<<<std::min(div_up(n, 256), sms * 8), 256, 0, st>>>(
+            l, s->lvl.as<int>(), s->lvl_nodes.as<int>(), s->spos.as<float2>(), s->nd_first.as<int>(),
+            s->nd_count.as<int>(), s->nd_skip.as<int>(), s->box.as<float>(), s->nd_sum.as<float2>(),
+            s->nd_rec.as<float4>(), s->nd_aux.as<int2>());
+    BL_CUDA_TRY(cudaGetLastError());
+    return BL_OK;
+}
+
+// repulsion sums of every vertex from the tree of S, neighbours taken out
+static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaStream_t st) {
+    BHState* s = L->bh;
+    const int n = L->g->n;
+    BL_CUDA_TRY(cudaMemsetAsync(s->walkcnt.p, 0, 2 * sizeof(unsigned long long), st));
+    const float th = theta;
+    const float theta2 = th * th;
+    walk_kernel<<<div_up(n, 256), 256, 0, st>>>(s->vals0.as<int>(), s->spos.as<float2>(), s->cnt.as<int>(),
+                                                n, s->nd_rec.as<float4>(), s->nd_aux.as<int2>(), theta2,
+                                                s->rep.as<float2>(), s->walkcnt.as<unsigned long long>());
+    if (!L->prm.repulse_neighbors)
+        nbr_correct_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+            L->g->rowptr.as<int>(), L->g->colids.as<int>(), S, n, s->rep.as<float2>());
+    BL_CUDA_TRY(cudaGetLastError());
+    return BL_OK;
+}
+
+// predecessor batches of each batch (distinct earlier batches holding a neighbour
+// of one of its rows), most recent first
+static bl_status bh_preds(bl_layout* L, int BS) {
+    BHState* s = L->bh;
+    if (s->preds_bs == BS) return BL_OK;
+    const bl_graph* g = L->g;
+    const int n = g->n, B = div_up(n, BS);
+    std::vector<int> ptr(B + 1, 0), lst, mark(B, -1);
+    lst.reserve((size_t)B * 8);
+    for (int b = 0; b < B; b++) {
+        const int lo = b * BS, hi = std::min(n, lo + BS);
+        const size_t start = lst.size();
+        for (int i = lo; i < hi; i++)
+            for (int k = g->h_rowptr[i]; k < g->h_rowptr[i + 1]; k++) {
+                const int bj = g->h_colids[k] / BS;
+                if (bj < b && mark[bj] != b) {
+                    mark[bj] = b;
+                    lst.push_back(bj);
+                }
+            }
+        std::sort(lst.begin() + start, lst.end(), std::greater<int>());
+        ptr[b + 1] = (int)lst.size();
+    }
+    const Allocator& al = L->alloc;
+    BL_TRY(s->preds_ptr.ensure(al, (size_t)(B + 1) * 4));
+    BL_TRY(s->preds.ensure(al, std::max<size_t>(lst.size(), 1) * 4));
+    BL_TRY(s->flags.ensure(al, (size_t)B * 4));
+    BL_TRY(s->epart.ensure(al, (size_t)B * 8));
+    cudaStream_t st = current_stream();
+    BL_CUDA_TRY(cudaMemcpyAsync(s->preds_ptr.p, ptr.data(), (size_t)(B + 1) * 4, cudaMemcpyHostToDevice, st));
+    if (!lst.empty())
+        BL_CUDA_TRY(cudaMemcpyAsync(s->preds.p, lst.data(), lst.size() * 4, cudaMemcpyHostToDevice, st));
+    BL_CUDA_TRY(cudaMemsetAsync(s->flags.p, 0, (size_t)B * 4, st));
+    BL_CUDA_TRY(cudaStreamSynchronize(st));
+    s->preds_bs = BS;
+    s->B = B;
+    s->stamp = 0;
+    return BL_OK;
+}
+
+bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) {
+    BL_TRY(bh_ensure(L));
+    BL_TRY(bh_preds(L, BS));
+    BHState* s = L->bh;
+    const int n = L->g->n;
+    BL_TRY(L->pos2.ensure(L->alloc, (size_t)n * sizeof(float2)));
+    BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(iters, 1) * sizeof(double)));
+    double step = 1.0;
+    for (int64_t k = 0; k < L->t; k++) step *= 0.999;
+    int occ = 0;
+    BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel, kSweepThreads, 0));
+    const int G = std::min(s->B, std::max(1, occ) * device_sm_count());
+    for (int t = 0; t < iters; t++) {
+        const float2* S = L->pos.as<float2>();
+        float2* bnew = L->pos2.as<float2>();
+        BL_TRY(bh_build(L, S, st));
+        BL_TRY(bh_repulsion(L, S, theta, st));
+        SweepArgs a{};
+        a.rowptr = L->g->rowptr.as<int>();
+        a.colids = L->g->colids.as<int>();
+        a.bold = S;
+        a.bnew = bnew;
+        a.rep = s->rep.as<float2>();
+        a.flags = s->flags.as<int>();
+        a.preds_ptr = s->preds_ptr.as<int>();
+        a.preds = s->preds.as<int>();
+        a.epart = s->epart.as<double>();
+        a.status = static_cast<int*>(L->status.p);
+        a.n = n;
+        a.BS = BS;
+        a.B = s->B;
+        a.stamp = ++s->stamp;
+        a.invK = 1.0f / L->prm.K;
+        a.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
+        a.stepf = (float)step;
+        void* args[] = {&a};
+        BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(G), dim3(kSweepThreads),
+                                                args, 0, st));
+        batch_energy_kernel<<<1, 32, 0, st>>>(s->epart.as<double>(), s->B, L->energy.as<double>() + t);
+        BL_CUDA_TRY(cudaGetLastError());
+        std::swap(L->pos, L->pos2);
+        step *= 0.999;
+    }
+    // interaction counts of the last iteration
+    unsigned long long c[2] = {0, 0};
+    BL_CUDA_TRY(cudaMemcpyAsync(c, s->walkcnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    BL_CUDA_TRY(cudaStreamSynchronize(st));
+    L->far_nodes = (double)c[0];
+    L->near_pairs = (double)c[1];
+    return BL_OK;
+}
+
+bl_status bh_debug_forces(bl_layout* L, float theta, float2* f_out, cudaStream_t st) {
+    BL_TRY(bh_ensure(L));
+    const int n = L->g->n;
+    const float2* S = L->pos.as<float2>();
+    BL_TRY(bh_build(L, S, st));
+    BL_TRY(bh_repulsion(L, S, theta, st));
+    bh_snapshot_force_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+        L->g->rowptr.as<int>(), L->g->colids.as<int>(), S, n, L->bh->rep.as<float2>(), 1.0f / L->prm.K,
+        -L->prm.R * L->prm.K * L->prm.K, f_out);
+    BL_CUDA_TRY(cudaGetLastError());
+    unsigned long long c[2] = {0, 0};
+    BL_CUDA_TRY(cudaMemcpyAsync(c, L->bh->walkcnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    BL_CUDA_TRY(cudaStreamSynchronize(st));
+    L->far_nodes = (double)c[0];
+    L->near_pairs = (double)c[1];
+    return BL_OK;
+}
+
+bl_status bh_debug_tree(bl_layout* L, uint32_t* codes, int32_t* perm, int32_t* first, int32_t* count,
+                        int32_t* level, int32_t* skip, float* sumx, float* sumy, int64_t cap,
+                        int64_t* nnodes, float* box, cudaStream_t st) {
+    BL_TRY(bh_ensure(L));
+    BHState* s = L->bh;
+    const int n = L->g->n;
+    BL_TRY(bh_build(L, L->pos.as<float2>(), st));
+    int M = 0;
+    BL_CUDA_TRY(cudaMemcpyAsync(&M, s->cnt.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BL_CUDA_TRY(cudaStreamSynchronize(st));
+    *nnodes = M;
+    if (box) {
+        float b[3];
+        BL_CUDA_TRY(cudaMemcpy(b, s->box.p, sizeof(b), cudaMemcpyDeviceToHost));
+        box[0] = b[0];
+        box[1] = b[1];
+        box[2] = b[2];
+    }
+    if (codes) BL_CUDA_TRY(cudaMemcpy(codes, s->keys0.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    if (perm) BL_CUDA_TRY(cudaMemcpy(perm, s->vals0.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    if (M > cap) return set_error(BL_EINVAL, "bl_debug_bh_tree: node arrays too small");
+    if (first) BL_CUDA_TRY(cudaMemcpy(first, s->nd_first.p, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (count) BL_CUDA_TRY(cudaMemcpy(count, s->nd_count.p, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (level) BL_CUDA_TRY(cudaMemcpy(level, s->nd_level.p, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (skip) BL_CUDA_TRY(cudaMemcpy(skip, s->nd_skip.p, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (sumx || sumy) {
+        std::vector<float2> sm((size_t)M);
+        BL_CUDA_TRY(cudaMemcpy(sm.data(), s->nd_sum.p, (size_t)M * sizeof(float2), cudaMemcpyDeviceToHost));
+        for (int v = 0; v < M; v++) {
+            if (sumx) sumx[v] = sm[v].x;
+            if (sumy) sumy[v] = sm[v].y;
+        }
+    }
+    return BL_OK;
+}
+
 }  // namespace bl
