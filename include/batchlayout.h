@@ -225,10 +225,13 @@ bl_status bl_debug_bh_tree(bl_layout *L, uint32_t *codes, int32_t *perm, int32_t
  * published by all CTAs, 2 column tile in shared memory, 3 bulk warps done with
  * the previous step, 4 critical rows moved, 6 arrival posted}; bulk warps {7
  * step start, 5 moved rows picked up, 10 neighbours staged, 8 step done};
- * slots 9 and 11 unused (0). */
+ * slots 9 and 11 unused (0). In BH mode (any max_steps > 0) the last
+ * iteration's sweep is traced instead: the start time of each of its dependency
+ * levels, then its end. */
 bl_status bl_set_trace(bl_layout *L, int32_t max_steps);
 
-/* Copies the trace of the last traced run: [CTAs][max_steps][12] uint64.
+/* Copies the trace of the last traced run: [CTAs][max_steps][12] uint64
+ * (exact mode) or [levels + 1] uint64 (BH mode).
  * *count = entries; with out == NULL only the count. Synchronises. */
 bl_status bl_get_trace(const bl_layout *L, uint64_t *out, int64_t cap, int64_t *count);
 

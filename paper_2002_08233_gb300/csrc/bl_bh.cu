@@ -66,11 +66,10 @@ struct BHState {
     DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
     DevBuf walkcnt;                     // unsigned long long[2]: far nodes, near pairs
     // sweep
-    int preds_bs = -1, B = 0;
-    DevBuf flags;                       // int[B]: iteration stamp of the last update
-    DevBuf preds_ptr, preds;            // predecessor batches, most recent first
-    DevBuf epart;                       // double[B] energy per batch
-    int stamp = 0;
+    int plan_bs = -1, nlevels = 0, nbig = 0;
+    DevBuf split, bigrows, old;         // row split points, rows with many old edges, old attraction
+    DevBuf lvl_ptr, tasks, seg_off, seg_sum, seg_cnt;   // level-set schedule
+    DevBuf e_row, epart;                // per-row |ct|^2, reduction partials
 };
 
 void bh_state_free(BHState* s) {
@@ -78,7 +77,8 @@ void bh_state_free(BHState* s) {
     DevBuf* bufs[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->hist, &s->scan_part,
                       &s->bpart, &s->box, &s->cnt, &s->spos, &s->nd_first, &s->nd_count,
                       &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
-                      &s->lvl_nodes, &s->rep, &s->walkcnt, &s->flags, &s->preds_ptr, &s->preds,
+                      &s->lvl_nodes, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->old,
+                      &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->seg_cnt, &s->e_row,
                       &s->epart};
     for (DevBuf* b : bufs) b->release();
     delete s;
@@ -577,106 +577,203 @@ __global__ void bh_snapshot_force_kernel(const int* __restrict__ rowptr, const i
 // minibatch sweep (Algorithm S5's batch loop)
 // ---------------------------------------------------------------------------
 
+// Attraction of row i from its neighbours in its own or later minibatches: they
+// have not moved yet when i's minibatch runs, so this part uses the snapshot S
+// and is computed for all rows before the sweep (warp per row; rows with more
+// than kBigRow such edges get a whole block from attr_old_big_kernel).
+constexpr int kBigRow = 8192;
+
+__device__ __forceinline__ void attr_term(float2 me, float2 p, float invK, float& ax, float& ay) {
+    const float dx = p.x - me.x, dy = p.y - me.y;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
+    const float sc = d2 * rsqrt_sfu(d2) * invK;
+    ax = fmaf(dx, sc, ax);
+    ay = fmaf(dy, sc, ay);
+}
+
+// lane-strided sum over edges [e0, e1) of row `me`, 4 loads in flight per lane
+__device__ __forceinline__ void attr_sum_strided(const int* __restrict__ colids,
+                                                 const float2* __restrict__ S, float2 me, int e0,
+                                                 int e1, int start, int stride, float invK,
+                                                 float& ax, float& ay) {
+    for (int e = e0 + start; e < e1; e += 4 * stride) {
+        int j[4];
+        float2 p[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) j[k] = e + k * stride < e1 ? __ldg(&colids[e + k * stride]) : -1;
+#pragma unroll
+        for (int k = 0; k < 4; k++) p[k] = j[k] >= 0 ? S[j[k]] : me;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (j[k] >= 0) attr_term(me, p[k], invK, ax, ay);
+    }
+}
+
+__global__ void attr_old_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
+                                const int* __restrict__ split, const float2* __restrict__ S, int n,
+                                float invK, float2* __restrict__ old) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int i = warp;
+    const int e0 = split[i], e1 = rowptr[i + 1];
+    if (e1 - e0 > kBigRow) return;   // attr_old_big_kernel
+    const float2 me = S[i];
+    float ax = 0.f, ay = 0.f;
+    attr_sum_strided(colids, S, me, e0, e1, lane, 32, invK, ax, ay);
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) old[i] = make_float2(ax, ay);
+}
+
+__global__ void __launch_bounds__(1024) attr_old_big_kernel(
+    const int* __restrict__ rowptr, const int* __restrict__ colids, const int* __restrict__ split,
+    const float2* __restrict__ S, const int* __restrict__ big_rows, float invK,
+    float2* __restrict__ old) {
+    __shared__ float2 s_w[32];
+    const int i = big_rows[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float2 me = S[i];
+    float ax = 0.f, ay = 0.f;
+    attr_sum_strided(colids, S, me, split[i], rowptr[i + 1], threadIdx.x, blockDim.x, invK, ax, ay);
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) s_w[warp] = make_float2(ax, ay);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sx = 0.f, sy = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            sx += s_w[w].x;
+            sy += s_w[w].y;
+        }
+        old[i] = make_float2(sx, sy);
+    }
+}
+
+// Level sets of the sweep. Row i reads its neighbours in earlier minibatches at
+// their new positions, so it can run once they have moved; its neighbours in its
+// own or later minibatches are read at the snapshot, whatever the order. With
+// level(i) = 1 + max level of i's earlier-minibatch neighbours (1 when there are
+// none), all rows of one level are independent of each other and depend only on
+// lower levels: running the levels in order, one grid barrier apart, computes
+// exactly the sequential minibatch sweep. A row with many earlier-minibatch edges
+// is cut into segments (tasks); the last segment to finish combines the segment
+// sums in order.
 struct SweepArgs {
     const int* rowptr;
     const int* colids;
     const float2* bold;      // positions at iteration start (S)
     float2* bnew;            // positions after this iteration's update
     const float2* rep;       // repulsion sums (unscaled)
-    int* flags;
-    const int* preds_ptr;
-    const int* preds;
-    double* epart;
+    const float2* old;       // attraction from not-yet-moved neighbours
+    const int* lvl_ptr;      // tasks of level l: [lvl_ptr[l], lvl_ptr[l+1])
+    const int4* tasks;       // {row, first edge, end edge, segment | nseg << 16}
+    const int* seg_off;      // per row: offset of its segment sums (rows with nseg > 1)
+    float2* seg_sum;
+    int* seg_cnt;            // per row: segments finished (reset per launch)
+    double* e_row;           // |ct|^2 of every row
+    unsigned* bar;
     int* status;
-    int n, BS, B, stamp;
+    int nlevels;
     float invK, negRK2, stepf;
+    unsigned long long* trace;   // optional: start time of each level (CTA 0)
 };
 
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
-    constexpr int W = kSweepThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ double s_e[W];
-    __shared__ int s_ok;
-    for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
-        // wait for every earlier batch this batch's rows have edges into (bounded)
-        if (warp == 0) {
-            int ok = 1;
-            const unsigned long long t0 = global_ns();
-            for (int p = a.preds_ptr[b] + lane; p < a.preds_ptr[b + 1]; p += 32) {
-                const int* f = a.flags + a.preds[p];
-                unsigned spin = 0;
-                while (ok) {
-                    if (ld_volatile_i32(f) >= a.stamp) break;
-                    if ((++spin & 255u) == 0u) {
-                        if (ld_volatile_i32(a.status) != 0) ok = 0;
-                        else if (global_ns() - t0 > kWaitLimitNs) {
-                            atomicCAS(a.status, 0, (int)BL_ETIMEOUT);
-                            ok = 0;
-                        }
-                    }
-                }
-            }
-            ok = __all_sync(0xffffffffu, ok);
-            __threadfence();   // acquire side: the flags seen above order the loads below
-            if (lane == 0) s_ok = ok;
+constexpr int kSegEdges = 1024;   // earlier-minibatch edges per task
+
+__device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float sx, float sy) {
+    const float2 me = a.bold[i];
+    const float2 rp = a.rep[i];
+    const float2 od = a.old[i];
+    const float fx = fmaf(a.negRK2, rp.x, sx + od.x);
+    const float fy = fmaf(a.negRK2, rp.y, sy + od.y);
+    float nx = me.x, ny = me.y, gx = fx, gy = fy;
+    float n2 = fmaf(gx, gx, gy * gy);
+    if (n2 > 0.f) {
+        if (!(n2 < INFINITY)) {
+            gx *= 0x1p-64f;
+            gy *= 0x1p-64f;
+            n2 = fmaf(gx, gx, gy * gy);
         }
-        __syncthreads();
-        if (!s_ok) return;
-        const int lo = b * a.BS, hi = min(a.n, lo + a.BS);
-        double e_acc = 0.0;
-        for (int i = lo + warp; i < hi; i += W) {
+        const float sc = a.stepf * rsqrt_sfu(n2);
+        nx = fmaf(sc, gx, me.x);
+        ny = fmaf(sc, gy, me.y);
+    }
+    a.bnew[i] = make_float2(nx, ny);
+    a.e_row[i] = (double)fmaf(fx, fx, fy * fy);
+}
+
+__global__ void __launch_bounds__(kSweepThreads) level_sweep_kernel(SweepArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    GridBarrier bar{a.bar, a.status, gridDim.x, 0u};
+    for (int l = 0; l < a.nlevels; l++) {
+        if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[l] = global_ns();
+        for (int t = a.lvl_ptr[l] + gw; t < a.lvl_ptr[l + 1]; t += nw) {
+            const int4 tk = a.tasks[t];
+            const int i = tk.x;
+            const int seg = tk.w & 0xFFFF, nseg = tk.w >> 16;
             const float2 me = a.bold[i];
-            float ax = 0.f, ay = 0.f;
-            const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
-            for (int e = e0 + lane; e < e1; e += 32) {
-                const int j = a.colids[e];
-                const float2 p = j < lo ? __ldcg(&a.bnew[j]) : a.bold[j];
-                const float dx = p.x - me.x, dy = p.y - me.y;
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-                const float s = d2 * rsqrt_sfu(d2) * a.invK;
-                ax = fmaf(dx, s, ax);
-                ay = fmaf(dy, s, ay);
+            float sx = 0.f, sy = 0.f;
+            for (int e = tk.y + lane; e < tk.z; e += 128) {   // 4 gathers in flight per lane
+                int j[4];
+                float2 p[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) j[k] = e + 32 * k < tk.z ? __ldg(&a.colids[e + 32 * k]) : -1;
+#pragma unroll
+                for (int k = 0; k < 4; k++) p[k] = j[k] >= 0 ? __ldcg(&a.bnew[j[k]]) : me;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (j[k] >= 0) attr_term(me, p[k], a.invK, sx, sy);
             }
-            ax = warp_sum(ax);
-            ay = warp_sum(ay);
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
             if (lane == 0) {
-                const float2 r = a.rep[i];
-                const float fx = fmaf(a.negRK2, r.x, ax);
-                const float fy = fmaf(a.negRK2, r.y, ay);
-                float nx = me.x, ny = me.y, gx = fx, gy = fy;
-                float n2 = fmaf(gx, gx, gy * gy);
-                if (n2 > 0.f) {
-                    if (!(n2 < INFINITY)) {
-                        gx *= 0x1p-64f;
-                        gy *= 0x1p-64f;
-                        n2 = fmaf(gx, gx, gy * gy);
+                if (nseg <= 1) {
+                    finish_row(a, i, sx, sy);
+                } else {
+                    const int off = a.seg_off[i];
+                    a.seg_sum[off + seg] = make_float2(sx, sy);
+                    __threadfence();
+                    if (atomicAdd(&a.seg_cnt[i], 1) == nseg - 1) {
+                        __threadfence();
+                        float tx = 0.f, ty = 0.f;
+                        for (int q = 0; q < nseg; q++) {   // segments in order
+                            const float2 v = __ldcg(&a.seg_sum[off + q]);
+                            tx += v.x;
+                            ty += v.y;
+                        }
+                        finish_row(a, i, tx, ty);
                     }
-                    const float sc = a.stepf * rsqrt_sfu(n2);
-                    nx = fmaf(sc, gx, me.x);
-                    ny = fmaf(sc, gy, me.y);
                 }
-                a.bnew[i] = make_float2(nx, ny);
-                e_acc += (double)fmaf(fx, fx, fy * fy);
             }
         }
-        if (lane == 0) s_e[warp] = e_acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double e = 0.0;
-            for (int w = 0; w < W; w++) e += s_e[w];
-            a.epart[b] = e;
-            __threadfence();
-            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a.flags + b), "r"(a.stamp)
-                         : "memory");
-        }
-        __syncthreads();
+        if (!bar.sync()) return;
+    }
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[a.nlevels] = global_ns();
+}
+
+// energy of the iteration: fixed-order reduction of the rows' |ct|^2
+__global__ void row_energy_kernel(const double* __restrict__ e_row, int n, double* __restrict__ part) {
+    __shared__ double s_w[32];
+    double e = 0.0;
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * per, hi = min(n, lo + per);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) e += e_row[i];
+    e = warp_sum_d(e);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+        part[blockIdx.x] = t;
     }
 }
 
-__global__ void batch_energy_kernel(const double* __restrict__ epart, int B, double* __restrict__ out) {
-    // one warp, fixed order
+__global__ void energy_parts_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
     double e = 0.0;
-    for (int b = threadIdx.x; b < B; b += 32) e += epart[b];
+    for (int b = threadIdx.x; b < np; b += 32) e += part[b];
     e = warp_sum_d(e);
     if (threadIdx.x == 0) *out = e;
 }
@@ -781,49 +878,83 @@ static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaSt
     return BL_OK;
 }
 
-// predecessor batches of each batch (distinct earlier batches holding a neighbour
-// of one of its rows), most recent first
-static bl_status bh_preds(bl_layout* L, int BS) {
+// Per (graph, minibatch size): the split point of every row (first edge into its
+// own or a later minibatch), the rows with many such edges, the level of every
+// row and the sweep's tasks grouped by level.
+static bl_status bh_plan(bl_layout* L, int BS) {
     BHState* s = L->bh;
-    if (s->preds_bs == BS) return BL_OK;
+    if (s->plan_bs == BS) return BL_OK;
     const bl_graph* g = L->g;
-    const int n = g->n, B = div_up(n, BS);
-    std::vector<int> ptr(B + 1, 0), lst, mark(B, -1);
-    lst.reserve((size_t)B * 8);
-    for (int b = 0; b < B; b++) {
-        const int lo = b * BS, hi = std::min(n, lo + BS);
-        const size_t start = lst.size();
-        for (int i = lo; i < hi; i++)
-            for (int k = g->h_rowptr[i]; k < g->h_rowptr[i + 1]; k++) {
-                const int bj = g->h_colids[k] / BS;
-                if (bj < b && mark[bj] != b) {
-                    mark[bj] = b;
-                    lst.push_back(bj);
-                }
-            }
-        std::sort(lst.begin() + start, lst.end(), std::greater<int>());
-        ptr[b + 1] = (int)lst.size();
+    const int n = g->n;
+    const int* rp = g->h_rowptr.data();
+    const int* ci = g->h_colids.data();
+    std::vector<int> split(n), level(n), bigrows;
+    int nlev = 0;
+    for (int i = 0; i < n; i++) {
+        const int lo = (i / BS) * BS;
+        const int* sp = std::lower_bound(ci + rp[i], ci + rp[i + 1], lo);
+        split[i] = (int)(sp - ci);
+        if (ci + rp[i + 1] - sp > kBigRow) bigrows.push_back(i);
+        int d = 0;
+        for (const int* c = ci + rp[i]; c < sp; c++) d = std::max(d, level[*c]);
+        level[i] = d + 1;
+        nlev = std::max(nlev, d + 1);
+    }
+    // tasks by level (rows in id order inside a level), big rows cut into segments
+    std::vector<int> lcount(nlev + 1, 0);
+    std::vector<int> nseg(n);
+    for (int i = 0; i < n; i++) {
+        const int nd = split[i] - rp[i];
+        nseg[i] = std::max(1, div_up(nd, kSegEdges));
+        lcount[level[i]] += nseg[i];
+    }
+    std::vector<int> lvl_ptr(nlev + 1, 0);   // levels 1..nlev -> slots 0..nlev-1
+    for (int l = 1; l <= nlev; l++) lvl_ptr[l] = lvl_ptr[l - 1] + lcount[l];
+    std::vector<int> fill(lvl_ptr.begin(), lvl_ptr.end() - 1);
+    std::vector<int4> tasks((size_t)lvl_ptr[nlev]);
+    std::vector<int> seg_off(n, 0);
+    int nsegsum = 0;
+    for (int i = 0; i < n; i++) {
+        const int ns = nseg[i];
+        if (ns > 1) {
+            seg_off[i] = nsegsum;
+            nsegsum += ns;
+        }
+        const int e0 = rp[i], e1 = split[i];
+        for (int q = 0; q < ns; q++) {
+            const int a0 = e0 + (int)((int64_t)(e1 - e0) * q / ns);
+            const int a1 = e0 + (int)((int64_t)(e1 - e0) * (q + 1) / ns);
+            tasks[fill[level[i] - 1]++] = make_int4(i, a0, a1, q | (ns << 16));
+        }
+        if (ns >= 65536) return set_error(BL_EINVAL, "Barnes-Hut sweep: row too long");
     }
     const Allocator& al = L->alloc;
-    BL_TRY(s->preds_ptr.ensure(al, (size_t)(B + 1) * 4));
-    BL_TRY(s->preds.ensure(al, std::max<size_t>(lst.size(), 1) * 4));
-    BL_TRY(s->flags.ensure(al, (size_t)B * 4));
-    BL_TRY(s->epart.ensure(al, (size_t)B * 8));
     cudaStream_t st = current_stream();
-    BL_CUDA_TRY(cudaMemcpyAsync(s->preds_ptr.p, ptr.data(), (size_t)(B + 1) * 4, cudaMemcpyHostToDevice, st));
-    if (!lst.empty())
-        BL_CUDA_TRY(cudaMemcpyAsync(s->preds.p, lst.data(), lst.size() * 4, cudaMemcpyHostToDevice, st));
-    BL_CUDA_TRY(cudaMemsetAsync(s->flags.p, 0, (size_t)B * 4, st));
+    auto up = [&](DevBuf& d, const void* h, size_t bytes) -> bl_status {
+        BL_TRY(d.ensure(al, std::max<size_t>(bytes, 16)));
+        if (bytes) BL_CUDA_TRY(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, st));
+        return BL_OK;
+    };
+    BL_TRY(up(s->split, split.data(), split.size() * 4));
+    BL_TRY(up(s->bigrows, bigrows.data(), bigrows.size() * 4));
+    BL_TRY(up(s->lvl_ptr, lvl_ptr.data(), lvl_ptr.size() * 4));
+    BL_TRY(up(s->tasks, tasks.data(), tasks.size() * sizeof(int4)));
+    BL_TRY(up(s->seg_off, seg_off.data(), seg_off.size() * 4));
+    BL_TRY(s->seg_sum.ensure(al, (size_t)std::max(nsegsum, 1) * sizeof(float2)));
+    BL_TRY(s->seg_cnt.ensure(al, (size_t)n * 4));
+    BL_TRY(s->e_row.ensure(al, (size_t)n * 8));
+    BL_TRY(s->epart.ensure(al, 1024 * 8));
+    BL_TRY(s->old.ensure(al, (size_t)n * sizeof(float2)));
     BL_CUDA_TRY(cudaStreamSynchronize(st));
-    s->preds_bs = BS;
-    s->B = B;
-    s->stamp = 0;
+    s->nbig = (int)bigrows.size();
+    s->nlevels = nlev;
+    s->plan_bs = BS;
     return BL_OK;
 }
 
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) {
     BL_TRY(bh_ensure(L));
-    BL_TRY(bh_preds(L, BS));
+    BL_TRY(bh_plan(L, BS));
     BHState* s = L->bh;
     const int n = L->g->n;
     BL_TRY(L->pos2.ensure(L->alloc, (size_t)n * sizeof(float2)));
@@ -831,35 +962,56 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
     double step = 1.0;
     for (int64_t k = 0; k < L->t; k++) step *= 0.999;
     int occ = 0;
-    BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel, kSweepThreads, 0));
-    const int G = std::min(s->B, std::max(1, occ) * device_sm_count());
+    BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_sweep_kernel, kSweepThreads, 0));
+    const int G = std::max(1, std::min(occ, 4)) * device_sm_count();
+    const int nep = std::min(1024, div_up(n, 1024));
     for (int t = 0; t < iters; t++) {
         const float2* S = L->pos.as<float2>();
         float2* bnew = L->pos2.as<float2>();
         BL_TRY(bh_build(L, S, st));
         BL_TRY(bh_repulsion(L, S, theta, st));
+        // attraction from neighbours that have not moved yet, all rows at once
+        attr_old_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K,
+            s->old.as<float2>());
+        if (s->nbig > 0)
+            attr_old_big_kernel<<<s->nbig, 1024, 0, st>>>(L->g->rowptr.as<int>(), L->g->colids.as<int>(),
+                                                          s->split.as<int>(), S, s->bigrows.as<int>(),
+                                                          1.0f / L->prm.K, s->old.as<float2>());
+        BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, st));
+        BL_TRY(layout_reset_sync_words(L, st));
         SweepArgs a{};
         a.rowptr = L->g->rowptr.as<int>();
         a.colids = L->g->colids.as<int>();
         a.bold = S;
         a.bnew = bnew;
         a.rep = s->rep.as<float2>();
-        a.flags = s->flags.as<int>();
-        a.preds_ptr = s->preds_ptr.as<int>();
-        a.preds = s->preds.as<int>();
-        a.epart = s->epart.as<double>();
+        a.old = s->old.as<float2>();
+        a.lvl_ptr = s->lvl_ptr.as<int>();
+        a.tasks = s->tasks.as<int4>();
+        a.seg_off = s->seg_off.as<int>();
+        a.seg_sum = s->seg_sum.as<float2>();
+        a.seg_cnt = s->seg_cnt.as<int>();
+        a.e_row = s->e_row.as<double>();
+        a.bar = layout_barrier_word(L);
         a.status = static_cast<int*>(L->status.p);
-        a.n = n;
-        a.BS = BS;
-        a.B = s->B;
-        a.stamp = ++s->stamp;
+        a.nlevels = s->nlevels;
         a.invK = 1.0f / L->prm.K;
         a.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
         a.stepf = (float)step;
+        a.trace = nullptr;
+        if (L->trace_steps > 0 && t == iters - 1) {   // trace the last iteration's sweep
+            const size_t tb = (size_t)(s->nlevels + 1) * sizeof(unsigned long long);
+            BL_TRY(L->trace.ensure(L->alloc, tb));
+            BL_CUDA_TRY(cudaMemsetAsync(L->trace.p, 0, tb, st));
+            a.trace = L->trace.as<unsigned long long>();
+            L->trace_count = s->nlevels + 1;
+        }
         void* args[] = {&a};
-        BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sweep_kernel, dim3(G), dim3(kSweepThreads),
-                                                args, 0, st));
-        batch_energy_kernel<<<1, 32, 0, st>>>(s->epart.as<double>(), s->B, L->energy.as<double>() + t);
+        BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)level_sweep_kernel, dim3(G),
+                                                dim3(kSweepThreads), args, 0, st));
+        row_energy_kernel<<<nep, 256, 0, st>>>(s->e_row.as<double>(), n, s->epart.as<double>());
+        energy_parts_kernel<<<1, 32, 0, st>>>(s->epart.as<double>(), nep, L->energy.as<double>() + t);
         BL_CUDA_TRY(cudaGetLastError());
         std::swap(L->pos, L->pos2);
         step *= 0.999;

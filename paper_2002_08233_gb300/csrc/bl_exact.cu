@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     const unsigned long long t0 = global_ns();
                     for (unsigned spin = 0;; ++spin) {
                         if ((int)(ld_acquire_u32(prm.bar) - target) >= 0) break;
+                        __nanosleep(32);   // 152 CTAs poll the same word
                         if ((spin & 255u) == 255u) {
                             if (ld_volatile_i32(prm.status) != 0) { ok = 0; break; }
                             if (global_ns() - t0 > kWaitLimitNs) {

@@ -155,6 +155,10 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
 bl_status exact_launch(const ExactPlan& plan, const ExactTask& task, const ExactParams& prm,
                        cudaStream_t st);
 
+// Status word, grid-barrier counter and their reset (bl_runtime.cu).
+bl_status layout_reset_sync_words(bl_layout* L, cudaStream_t st);
+unsigned* layout_barrier_word(bl_layout* L);
+
 // Per-iteration energies: energy[t] = sum over CTAs of e_iter[t][cta], in order.
 bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, cudaStream_t st);
 

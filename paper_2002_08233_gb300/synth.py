@@ -83,6 +83,17 @@ def uniform_positions(n: int, seed: int = 0) -> np.ndarray:
 # CSR assembly
 # ----------------------------------------------------------------------------
 
+def _sorted_unique(key: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + adjacent difference)."""
+    key = np.sort(key, kind="stable")
+    if key.size == 0:
+        return key
+    keep = np.empty(key.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(key[1:], key[:-1], out=keep[1:])
+    return key[keep]
+
+
 def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray, name: str = "") -> CSR:
     """Symmetrise, drop self-loops and duplicates, sort rows."""
     u = np.asarray(u, dtype=np.int64)
@@ -91,7 +102,7 @@ def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray, name: str = "") -> CSR:
     u, v = u[keep], v[keep]
     a = np.concatenate([u, v])
     b = np.concatenate([v, u])
-    key = np.unique(a * np.int64(n) + b)
+    key = _sorted_unique(a * np.int64(n) + b)
     rows = (key // n).astype(np.int64)
     cols = (key % n).astype(np.int32)
     counts = np.bincount(rows, minlength=n)
@@ -240,7 +251,7 @@ def erdos_renyi(n: int, mean_degree: float, seed: int) -> CSR:
         hi = np.maximum(a, b)
         ok = lo != hi
         cand = lo[ok] * np.int64(n) + hi[ok]
-        keys = np.unique(np.concatenate([keys, cand]))
+        keys = _sorted_unique(np.concatenate([keys, cand]))
     if keys.shape[0] > target:
         keys = rng.permutation(keys)[:target]
     return csr_from_edges(n, keys // n, keys % n, name=f"er{n}")
