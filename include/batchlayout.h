@@ -199,6 +199,33 @@ bl_status bl_serve_cancel(bl_server *S, uint64_t ticket);
 bl_status bl_server_stats(bl_server *S, double *out, int64_t cap);
 void bl_server_free(bl_server *S);
 
+/* ---- exact run without device allocations ------------------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * call cudaMalloc (an engine that hands out all device memory from its own pool,
+ * a serving loop that must not stall on an allocation's implicit
+ * synchronisation, a process under a hard device-memory quota).
+ * Runs `iters` exact-mode iterations (same engine as bl_layout_run with
+ * BL_EXACT) on buffers the caller owns, all device pointers: d_rowptr[n+1] and
+ * d_colids[nnz] a CSR that already satisfies bl_graph_load_csr's rules (not
+ * checked here), d_xy[2n] positions (in/out), d_energy[iters] per-iteration
+ * energy (out, may be NULL). params may be NULL (defaults as bl_layout_init);
+ * start_iter sets Step = 0.999^start_iter. Work goes to `stream` (a
+ * cudaStream_t, NULL = legacy default stream); the call synchronises it before
+ * returning and reports BL_ETIMEOUT from the device-side waits.
+ * Allocates nothing: the engine's working memory lives in one file-scope
+ * device array of about 2 MiB that every GPU loading the library holds until
+ * exit. Limits: n <= 131072 and iters x (CTAs, at most one per SM) <= 131072;
+ * larger requests return BL_EINVAL. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture. All calls share the array: calls that overlap on the
+ * GPU (other host threads, other streams) race and must be serialised by the
+ * caller. */
+bl_status bl_layout_run_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colids,
+                                float *d_xy, int32_t iters, int32_t batch,
+                                const bl_force_params *params, int64_t start_iter,
+                                double *d_energy, void *stream);
+
 /* ---- parity hooks ------------------------------------------------------------ */
 
 /* One-snapshot forces ct_i (FP32, 2 floats per vertex) for i in [lo, hi) from

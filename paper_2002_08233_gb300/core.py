@@ -83,6 +83,7 @@ def _declare(lib):
         "bl_debug_bh_tree": [P, P, P, P, P, P, P, P, P, i64, P, P],
         "bl_set_trace": [P, i32],
         "bl_get_trace": [P, P, i64, P],
+        "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name, None)
@@ -309,6 +310,19 @@ class Layout:
             self.close()
         except Exception:
             pass
+
+
+def layout_run_noalloc(n: int, d_rowptr: int, d_colids: int, d_xy: int, iters: int, batch: int = 256,
+                       K: float = 1.0, R: float = 1.0, repulse_neighbors: bool = False,
+                       start_iter: int = 0, d_energy: int = 0, stream: int = 0) -> None:
+    """bl_layout_run_noalloc on device buffers the caller owns (raw device
+    addresses): for callers that cannot allocate device memory. The library
+    keeps its working memory in a fixed device array; calls that overlap on the
+    GPU race on it."""
+    prm = ForceParams(K, R, int(repulse_neighbors), -1)
+    _check(load().bl_layout_run_noalloc(int(n), d_rowptr, d_colids, d_xy, int(iters), int(batch),
+                                        ctypes.byref(prm), int(start_iter), d_energy or None,
+                                        stream or None))
 
 
 def layout_batch(graphs, seeds, iters: int, batch: int = 64, mode: str = "exact",
