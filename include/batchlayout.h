@@ -155,12 +155,27 @@ void bl_layout_free(bl_layout *L);
 
 /* ---- quality (Section 3.7) --------------------------------------------------- */
 
-/* Stress (minimised over a uniform layout scale), neighbourhood preservation
- * and edge uniformity of the current positions, accumulated in FP64 on the GPU.
- * nsources <= 0: all-pairs stress; else that many BFS sources chosen by
- * SplitMix64(seed) without repeats. nqueries <= 0: every vertex is an NP query;
- * else a seeded sample. out[0..5] = {stress, scale s*, stress pairs, NP,
- * NP queries, edge uniformity}. Synchronises. */
+/* Layout quality as Section 3.7 measures it, of the current positions, in FP64
+ * on the GPU:
+ *  - stress sum_{pairs} (s*x_ij - d_ij)^2 / d_ij^2 at the scale s* that
+ *    minimises it (x = layout distance, d = BFS hop distance; unreachable pairs
+ *    skipped). nsources <= 0 or >= n: all unordered pairs. Otherwise the BFS
+ *    sources are a seeded sample (below) and the ordered-pair sum is scaled by
+ *    n / (2 nsources).
+ *  - neighbourhood preservation, 1-hop reading: for each query i with deg(i) > 0,
+ *    L_i = the deg(i) vertices nearest to i in the layout (squared distance in
+ *    FP64 as dx*dx + dy*dy, ties by smaller id); NP = mean of
+ *    |N(i) & L_i| / |N(i) | L_i|. nqueries <= 0 or >= n: every vertex; otherwise
+ *    a seeded sample drawn with seed ^ 0x5bd1e995.
+ *  - edge uniformity sqrt(sum_e (l_e - mean)^2 / (|E| mean^2)), each undirected
+ *    edge once.
+ * Seeded sample of m of n vertices: partial Fisher-Yates over 0..n-1 whose step
+ * k swaps entries k and k + (z_k mod (n-k)), z_k = SplitMix64 output k of the
+ * stream with state `seed` (as bl_layout_init); the sample is entries 0..m-1.
+ * out (cap >= 6 doubles) = {stress, s*, stress pairs, NP, NP queries with
+ * deg > 0, edge uniformity}; with cap >= 7, out[6] = total NP intersection size.
+ * Allocates scratch (O(n) for stress, 12 B x n per SM for NP) through the
+ * library allocator. Synchronises. */
 bl_status bl_quality(const bl_layout *L, int32_t nsources, int32_t nqueries, uint64_t seed,
                      double *out, int64_t cap);
 

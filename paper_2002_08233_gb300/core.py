@@ -255,11 +255,11 @@ class Layout:
         return {k: getattr(s, k) for k, _ in Stats._fields_}
 
     def quality(self, nsources: int = 0, nqueries: int = 0, seed: int = 0) -> dict:
-        out = np.zeros(6, dtype=np.float64)
+        out = np.zeros(7, dtype=np.float64)
         _check(_lib.bl_quality(self._h, int(nsources), int(nqueries), ctypes.c_uint64(seed),
                                _ptr(out), out.size))
         return {"stress": out[0], "scale": out[1], "stress_pairs": out[2], "np": out[3],
-                "np_queries": out[4], "edge_uniformity": out[5]}
+                "np_queries": out[4], "edge_uniformity": out[5], "np_intersections": out[6]}
 
     def debug_forces(self, mode: str = "exact", theta: float = THETA_DEFAULT, lo: int = 0,
                      hi: int | None = None) -> np.ndarray:

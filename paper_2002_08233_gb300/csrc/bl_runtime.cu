@@ -130,7 +130,7 @@ bl_status bh_debug_tree(bl_layout* L, uint32_t* codes, int32_t* perm, int32_t* f
                         int64_t cap, int64_t* nnodes, float* box, cudaStream_t st);
 // quality (bl_quality.cu)
 bl_status quality_run(bl_layout* L, int32_t nsources, int32_t nqueries, uint64_t seed,
-                      double* out, cudaStream_t st);
+                      double* out, int64_t cap, cudaStream_t st);
 
 static bool use_kahan(const bl_layout* L) {
     return L->prm.kahan > 0 || (L->prm.kahan < 0 && L->g->n >= (1 << 20));
@@ -461,7 +461,7 @@ bl_status bl_quality(const bl_layout* L, int32_t nsources, int32_t nqueries, uin
                      double* out, int64_t cap) {
     if (!L || !out) return set_error(BL_EINVAL, "bl_quality: NULL argument");
     if (cap < 6) return set_error(BL_EINVAL, "bl_quality: output needs 6 doubles");
-    return quality_run(const_cast<bl_layout*>(L), nsources, nqueries, seed, out, current_stream());
+    return quality_run(const_cast<bl_layout*>(L), nsources, nqueries, seed, out, cap, current_stream());
 }
 
 bl_status bl_debug_forces(bl_layout* L, bl_mode mode, float theta, int32_t lo, int32_t hi,

@@ -71,6 +71,18 @@ def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
     return z
 
 
+def seeded_sample(n: int, m: int, seed: int) -> np.ndarray:
+    """m distinct vertices of 0..n-1: entries 0..m-1 after a partial
+    Fisher-Yates shuffle whose step k swaps entries k and k + (z_k mod (n-k)),
+    z_k = SplitMix64 output k of the stream with state ``seed``."""
+    idx = np.arange(n, dtype=np.int64)
+    z = splitmix64(seed, m)
+    for k in range(m):
+        j = k + int(z[k] % np.uint64(n - k))
+        idx[k], idx[j] = idx[j], idx[k]
+    return idx[:m].astype(np.int32)
+
+
 def uniform_positions(n: int, seed: int = 0) -> np.ndarray:
     """float32[n, 2] uniform in [-1, 1): coordinate k (x of vertex i is k=2i,
     y is k=2i+1) is ((z_k >> 40) * 2^-24) * 2 - 1 for SplitMix64 output z_k."""

@@ -72,3 +72,17 @@ def test_small_graph_mix_sizes():
     gs = synth.small_graph_mix(count=60, seed=4)
     ns = np.array([g.n for g in gs])
     assert ns.min() >= 40 and ns.max() <= 5100
+
+
+def test_seeded_sample_is_distinct_and_seeded():
+    s = synth.seeded_sample(1000, 100, 7)
+    assert s.dtype == np.int32 and len(s) == 100
+    assert len(set(s.tolist())) == 100 and s.min() >= 0 and s.max() < 1000
+    assert np.array_equal(s, synth.seeded_sample(1000, 100, 7))
+    assert not np.array_equal(s, synth.seeded_sample(1000, 100, 8))
+    # step 0 swaps entry 0 with entry z_0 mod n
+    z0 = int(synth.splitmix64(7, 1)[0])
+    assert s[0] == z0 % 1000
+    # m = n gives a permutation
+    p = synth.seeded_sample(50, 50, 3)
+    assert sorted(p.tolist()) == list(range(50))
