@@ -191,6 +191,18 @@ bl_status bl_layout_batch(const bl_graph *const *gs, int32_t count, const uint64
                           int32_t iters, int32_t batch, bl_mode mode, float theta,
                           bl_layout **outs);
 
+/* Continues `count` existing layouts by `iters` exact-mode iterations each
+ * (Algorithm 2 per layout, Step continuing from each layout's own t), in the same
+ * batched launch as bl_layout_batch. Graphs of at most 16,384 vertices with
+ * batch <= 256 whose n^2 is at most the total work / SMs share the persistent
+ * kernel (one CTA per graph, positions in shared memory); the others run one at a
+ * time on the whole GPU. A graph's positions do not depend on which other graphs
+ * share the launch, nor on the launch shape the autotuner picks (first call per
+ * shared-memory size class; environment BL_BATCH_SHAPE=0..3 fixes it). The
+ * environment variable BL_BATCH_CHUNK sets the iterations per captured launch.
+ * Synchronises. */
+bl_status bl_layout_run_batch(bl_layout *const *Ls, int32_t count, int32_t iters, int32_t batch);
+
 /* ---- continuous-batching server -------------------------------------------- */
 
 /* A server owns a request thread and the device memory it admits against

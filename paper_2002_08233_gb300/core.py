@@ -84,6 +84,7 @@ def _declare(lib):
         "bl_set_trace": [P, i32],
         "bl_get_trace": [P, P, i64, P],
         "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
+        "bl_layout_run_batch": [P, i32, i32, i32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name, None)
@@ -336,6 +337,14 @@ def layout_batch(graphs, seeds, iters: int, batch: int = 64, mode: str = "exact"
     _check(lib.bl_layout_batch(hs, cnt, _ptr(sd), int(iters), int(batch), MODES[mode],
                                float(theta), outs))
     return [Layout(g, _handle=ctypes.c_void_p(outs[k])) for k, g in enumerate(graphs)]
+
+
+def run_batch(layouts, iters: int, batch: int = 64) -> None:
+    """Continues existing layouts in one batched launch (bl_layout_run_batch)."""
+    lib = load()
+    cnt = len(layouts)
+    hs = (ctypes.c_void_p * cnt)(*[L._h for L in layouts])
+    _check(lib.bl_layout_run_batch(hs, cnt, int(iters), int(batch)))
 
 
 class Server:

@@ -51,35 +51,6 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// CSR terms of one neighbour: attraction (d^2/K) (c_j - c_i)/d = (d/K)(c_j - c_i),
-// and, unless repulse_neighbors, the repulsion term the all-pairs sum gave this
-// neighbour, computed with exactly rep_pair's expressions so that it cancels.
-__device__ __forceinline__ void edge_terms(float xi, float yi, float2 p, float invK, bool rn,
-                                           float& ax, float& ay, float& qx, float& qy) {
-    const float dx = p.x - xi;
-    const float dy = p.y - yi;
-    const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-    const float a = d2 * rsqrt_sfu(d2) * invK;
-    ax = fmaf(dx, a, ax);
-    ay = fmaf(dy, a, ay);
-    if (!rn) {
-        const float inv = rcp_sfu(d2);
-        qx = fmaf(dx, inv, qx);
-        qy = fmaf(dy, inv, qy);
-    }
-}
-
-// ---- packed FP32x2 arithmetic (two columns per instruction) -----------------------
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk2(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-
 // Column tiles are stored in pairs: float4 q = (x_2q, x_2q+1, y_2q, y_2q+1).
 // The pair loop: rows m in [mlo, mhi) of the thread against the tile's first
 // 2*np columns; (XI, YI) hold each row's coordinates twice, (AX, AY) two partial

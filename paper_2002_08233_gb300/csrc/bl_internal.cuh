@@ -162,6 +162,31 @@ unsigned* layout_barrier_word(bl_layout* L);
 // Per-iteration energies: energy[t] = sum over CTAs of e_iter[t][cta], in order.
 bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, cudaStream_t st);
 
+// Whole-GPU exact run of one layout (bl_runtime.cu); the caller updates L's counters.
+bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_out, cudaStream_t st);
+
+// SplitMix64-seeded positions uniform in [-1, 1), as bl_layout_init draws them.
+void seeded_positions(int32_t n, uint64_t seed, float* xy);
+
+// A layout whose positions are uploaded from xy (2n floats) or drawn from seed,
+// without waiting for the upload (bl_runtime.cu). xy must stay valid until the
+// stream reaches the copy.
+bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
+                        const bl_force_params* params, bool sync, bl_layout** out);
+
+// ---------------------------------------------------------------------------
+// batched engine (bl_batch.cu)
+// ---------------------------------------------------------------------------
+
+constexpr int kBatchMaxN = 16384;   // largest graph one CTA holds in shared memory
+constexpr int kBatchMaxBS = 256;    // largest minibatch of the batched kernel
+
+// Exact iterations of many layouts: graphs within the limits above go into one
+// persistent launch per chunk of iterations (chunk <= 0: all at once), the rest
+// through exact_run one at a time. Updates the layouts' counters; synchronises.
+bl_status batch_run(bl_layout* const* Ls, int count, int iters, int BS, int chunk, cudaStream_t st,
+                    double* elapsed_ms);
+
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
@@ -276,6 +301,35 @@ struct GridBarrier {
         return s_ok != 0;
     }
 };
+
+// CSR terms of one neighbour: attraction (d^2/K) (c_j - c_i)/d = (d/K)(c_j - c_i),
+// and, unless repulse_neighbors, the repulsion term the all-pairs sum gave this
+// neighbour, computed with exactly rep_pair's expressions so that it cancels.
+__device__ __forceinline__ void edge_terms(float xi, float yi, float2 p, float invK, bool rn,
+                                           float& ax, float& ay, float& qx, float& qy) {
+    const float dx = p.x - xi;
+    const float dy = p.y - yi;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
+    const float a = d2 * rsqrt_sfu(d2) * invK;
+    ax = fmaf(dx, a, ax);
+    ay = fmaf(dy, a, ay);
+    if (!rn) {
+        const float inv = rcp_sfu(d2);
+        qx = fmaf(dx, inv, qx);
+        qy = fmaf(dy, inv, qy);
+    }
+}
+
+// ---- packed FP32x2 arithmetic (two columns per instruction) -----------------------
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
 
 }  // namespace bl
 #endif  // __CUDACC__

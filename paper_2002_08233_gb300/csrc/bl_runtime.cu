@@ -189,6 +189,48 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
 
 }  // namespace bl
 
+namespace bl {
+bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
+                        const bl_force_params* params, bool sync, bl_layout** out) {
+    if (!out) return set_error(BL_EINVAL, "bl_layout_init: out is NULL");
+    *out = nullptr;
+    if (!g) return set_error(BL_EINVAL, "bl_layout_init: NULL graph");
+    if (start_iter < 0) return set_error(BL_EINVAL, "bl_layout_init: start_iter < 0");
+    bl_force_params p{1.0f, 1.0f, 0, -1};
+    if (params) p = *params;
+    if (!(p.K > 0.0f) || !(p.R > 0.0f) || !std::isfinite(p.K) || !std::isfinite(p.R))
+        return set_error(BL_EINVAL, "bl_layout_init: K and R must be positive and finite");
+    bl_layout* L = new bl_layout();
+    L->g = g;
+    L->prm = p;
+    L->t = start_iter;
+    L->alloc = current_allocator();
+    bl_status s = L->pos.ensure(L->alloc, (size_t)g->n * sizeof(float2));
+    if (s == BL_OK) s = L->status.ensure(L->alloc, kStatusBytes);
+    if (s == BL_OK) {
+        std::vector<float> h;
+        const float* src = xy;
+        if (!src) {
+            h.resize((size_t)2 * g->n);
+            seeded_positions(g->n, seed, h.data());
+            src = h.data();
+        }
+        cudaStream_t st = current_stream();
+        cudaError_t e = cudaMemcpyAsync(L->pos.p, src, (size_t)g->n * sizeof(float2),
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L->status.p, 0, kStatusBytes, st);
+        if (e == cudaSuccess && (sync || !xy)) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_error(e, "bl_layout_init: upload");
+    }
+    if (s != BL_OK) {
+        bl_layout_free(L);
+        return s;
+    }
+    *out = L;
+    return BL_OK;
+}
+}  // namespace bl
+
 using namespace bl;
 
 extern "C" {
@@ -314,43 +356,9 @@ void bl_graph_free(bl_graph* g) {
 
 bl_status bl_layout_init(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
                          const bl_force_params* params, bl_layout** out) {
-    if (!out) return set_error(BL_EINVAL, "bl_layout_init: out is NULL");
-    *out = nullptr;
-    if (!g) return set_error(BL_EINVAL, "bl_layout_init: NULL graph");
-    if (start_iter < 0) return set_error(BL_EINVAL, "bl_layout_init: start_iter < 0");
-    bl_force_params p{1.0f, 1.0f, 0, -1};
-    if (params) p = *params;
-    if (!(p.K > 0.0f) || !(p.R > 0.0f) || !std::isfinite(p.K) || !std::isfinite(p.R))
-        return set_error(BL_EINVAL, "bl_layout_init: K and R must be positive and finite");
-    bl_layout* L = new bl_layout();
-    L->g = g;
-    L->prm = p;
-    L->t = start_iter;
-    L->alloc = current_allocator();
-    bl_status s = L->pos.ensure(L->alloc, (size_t)g->n * sizeof(float2));
-    if (s == BL_OK) s = L->status.ensure(L->alloc, kStatusBytes);
-    if (s == BL_OK) {
-        std::vector<float> h;
-        const float* src = xy;
-        if (!src) {
-            h.resize((size_t)2 * g->n);
-            seeded_positions(g->n, seed, h.data());
-            src = h.data();
-        }
-        cudaStream_t st = current_stream();
-        cudaError_t e = cudaMemcpyAsync(L->pos.p, src, (size_t)g->n * sizeof(float2),
-                                        cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(L->status.p, 0, kStatusBytes, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) s = cuda_error(e, "bl_layout_init: upload");
-    }
-    if (s != BL_OK) {
-        bl_layout_free(L);
-        return s;
-    }
-    *out = L;
-    return BL_OK;
+    return layout_create(g, xy, seed, start_iter, params, true, out);
 }
+
 
 bl_status bl_layout_set_positions(bl_layout* L, const float* xy, int64_t start_iter) {
     if (!L || !xy) return set_error(BL_EINVAL, "bl_layout_set_positions: NULL argument");

@@ -5,10 +5,6 @@
 using namespace bl;
 
 extern "C" {
-bl_status bl_layout_batch(const bl_graph* const*, int32_t, const uint64_t*, int32_t, int32_t,
-                          bl_mode, float, bl_layout**) {
-    return set_error(BL_EINVAL, "bl_layout_batch is not built yet");
-}
 bl_status bl_server_create(size_t, bl_server**) {
     return set_error(BL_EINVAL, "the server is not built yet");
 }
