@@ -205,25 +205,43 @@ bl_status bl_layout_run_batch(bl_layout *const *Ls, int32_t count, int32_t iters
 
 /* ---- continuous-batching server -------------------------------------------- */
 
-/* A server owns a request thread and the device memory it admits against
- * (mem_budget_bytes of working memory). */
+/* The paper lays out one graph per run; serving many requests is this library's
+ * addition. A server owns a worker thread and a stream on the device current at
+ * creation, and admits requests against mem_budget_bytes of working memory
+ * (positions, energies, Barnes-Hut trees; the graphs themselves belong to the
+ * caller). Each tick the worker admits queued requests in arrival order while
+ * they fit the budget (whole-GPU jobs also need one of 4 slots), then advances
+ * every admitted request: exact requests of at most 16,384 vertices and batch
+ * <= 256 share one persistent batched launch (50 iterations per tick); the
+ * others (larger exact, and BH) run a chunk whose length depends only on the
+ * request. A finished layout is copied to host memory and its device memory
+ * returns to the budget at once. A request's result does not depend on what
+ * else is being served. Device memory comes from the library allocator
+ * (bl_set_allocator) in force at each allocation. */
 bl_status bl_server_create(size_t mem_budget_bytes, bl_server **out);
 
-/* Queues a layout of g (which must stay alive until polled). mode BL_AUTO picks
- * exact below 50,000 vertices and BH above. BL_EBUDGET if the request could
- * never fit the budget. *ticket identifies the request. */
+/* Queues a layout of g (which must stay alive until polled) with seeded initial
+ * positions (as bl_layout_init), `iters` iterations of minibatch `batch`. mode
+ * BL_AUTO picks exact below 50,000 vertices and BH otherwise. BL_EBUDGET if the
+ * request could never fit the budget. *ticket identifies the request. */
 bl_status bl_serve_submit(bl_server *S, const bl_graph *g, uint64_t seed, int32_t iters,
                           int32_t batch, bl_mode mode, float theta, uint64_t *ticket);
 
-/* Non-blocking. BL_ENOTREADY until done; then copies 2n floats to xy (cap
- * checked) and the request's latency (submit -> done, seconds) and retires it. */
+/* Non-blocking. BL_ENOTREADY while queued or running; once done, copies 2n
+ * floats to xy (cap checked), the latency (submit -> done, seconds) to
+ * *latency_s, and retires the ticket. A canceled request answers BL_ECANCELED
+ * and a failed one its error (e.g. BL_ETIMEOUT), both retiring the ticket. */
 bl_status bl_serve_poll(bl_server *S, uint64_t ticket, float *xy, int64_t cap, double *latency_s);
 
-/* Cancels a queued request (BL_EBUSY once it is on the GPU). */
+/* Cancels a queued request (BL_EBUSY once it is on the GPU or finished). */
 bl_status bl_serve_cancel(bl_server *S, uint64_t ticket);
 
-/* out[0..5] = {completed, in flight, queued, bytes in use, p50 s, p99 s}. */
+/* out[0..5] = {completed, in flight, queued, bytes in use, p50 s, p99 s} over
+ * the requests completed so far; with cap >= 7, out[6] = peak bytes in use. */
 bl_status bl_server_stats(bl_server *S, double *out, int64_t cap);
+
+/* Stops the worker (requests still queued or running are dropped) and frees
+ * the server. */
 void bl_server_free(bl_server *S);
 
 /* ---- exact run without device allocations ------------------------------------ */

@@ -378,10 +378,10 @@ class Server:
         _check(_lib.bl_serve_cancel(self._h, ctypes.c_uint64(ticket)))
 
     def stats(self) -> dict:
-        out = np.zeros(6, dtype=np.float64)
+        out = np.zeros(7, dtype=np.float64)
         _check(_lib.bl_server_stats(self._h, _ptr(out), out.size))
         return {"completed": out[0], "in_flight": out[1], "queued": out[2], "bytes": out[3],
-                "p50_s": out[4], "p99_s": out[5]}
+                "p50_s": out[4], "p99_s": out[5], "peak_bytes": out[6]}
 
     def close(self):
         if getattr(self, "_h", None):

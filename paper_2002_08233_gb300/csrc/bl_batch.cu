@@ -377,10 +377,120 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
 
 }  // namespace
 
+// Jobs in persistent launches of at most `chunk` iterations; the launches are
+// captured once into a CUDA graph and replayed. Each launch's work list holds the
+// jobs with iterations left in that chunk, largest graph first.
+bl_status batch_launch(const BatchJob* jobs, int count, int chunk, cudaStream_t st) {
+    int max_it = 0, ncap = 1;
+    for (int k = 0; k < count; k++) {
+        if (jobs[k].L->g->n > kBatchMaxN || jobs[k].BS < 1 || jobs[k].BS > kBatchMaxBS)
+            return set_error(BL_EINVAL, "batched layout: graph or minibatch above the batched kernel's limits");
+        max_it = std::max(max_it, jobs[k].iters);
+        ncap = std::max(ncap, jobs[k].L->g->n);
+    }
+    if (count == 0 || max_it == 0) return BL_OK;
+    ncap = std::min((ncap + 63) / 64 * 64, kBatchMaxN);
+    if (chunk <= 0 || chunk > max_it) chunk = max_it;
+    const int nchunks = (max_it + chunk - 1) / chunk;
+    std::vector<int> order(count);
+    for (int k = 0; k < count; k++) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const int na = jobs[a].L->g->n, nb = jobs[b].L->g->n;
+        return na != nb ? na > nb : a < b;
+    });
+    const Allocator al = current_allocator();
+    std::vector<BatchItem> items;
+    std::vector<int> first(nchunks + 1, 0);
+    for (int j = 0; j < count; j++) {
+        bl_layout* L = jobs[j].L;
+        BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(jobs[j].iters, 1) * sizeof(double)));
+    }
+    for (int c = 0; c < nchunks; c++) {
+        first[c] = (int)items.size();
+        for (int j : order) {
+            const BatchJob& jb = jobs[j];
+            const int it0 = c * chunk;
+            if (it0 >= jb.iters) continue;
+            bl_layout* L = jb.L;
+            double step = 1.0;
+            for (int64_t q = 0; q < L->t + it0; q++) step *= 0.999;
+            BatchItem it{};
+            it.rowptr = L->g->rowptr.as<int>();
+            it.colids = L->g->colids.as<int>();
+            it.pos = L->pos.as<float2>();
+            it.energy = L->energy.as<double>() + it0;
+            it.step0 = step;
+            it.n = L->g->n;
+            it.BS = jb.BS;
+            it.iters = std::min(chunk, jb.iters - it0);
+            it.rn = L->prm.repulse_neighbors;
+            it.invK = 1.0f / L->prm.K;
+            it.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
+            items.push_back(it);
+        }
+    }
+    first[nchunks] = (int)items.size();
+    int shape = 0;
+    {
+        std::vector<BatchItem> sample(items.begin(), items.begin() + first[1]);
+        BL_TRY(autotune(ncap, sample, al, st, &shape));
+    }
+    DevBuf ditems, dnext;
+    bl_status s = ditems.ensure(al, items.size() * sizeof(BatchItem));
+    if (s == BL_OK) s = dnext.ensure(al, (size_t)nchunks * 16);
+    if (s == BL_OK) {
+        const cudaError_t e = cudaMemcpyAsync(ditems.p, items.data(), items.size() * sizeof(BatchItem),
+                                              cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) s = cuda_error(e, "batched layout: work list upload");
+    }
+    int grid = 0;
+    if (s == BL_OK) s = shape_grid(shape, ncap, first[1], &grid);
+    if (s == BL_OK) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int c = 0; c < nchunks && e == cudaSuccess; c++) {
+            unsigned* next = reinterpret_cast<unsigned*>(static_cast<char*>(dnext.p) + 16 * c);
+            e = cudaMemsetAsync(next, 0, sizeof(unsigned), cs);
+            BatchArgs args{ditems.as<BatchItem>() + first[c], first[c + 1] - first[c], next, ncap};
+            void* kargs[] = {&args};
+            if (e == cudaSuccess)
+                e = cudaLaunchKernel(kShapes[shape].fn, dim3(grid), dim3(kShapes[shape].T), kargs,
+                                     batch_smem_bytes(ncap), cs);
+        }
+        if (cs) {
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_error(e, "batched layout: graph launch");
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    ditems.release();
+    dnext.release();
+    if (s != BL_OK) return s;
+    for (int j = 0; j < count; j++) {
+        bl_layout* L = jobs[j].L;
+        const double n = (double)L->g->n;
+        const int it = jobs[j].iters;
+        L->last_iters = it;
+        L->t += it;
+        L->vupd += n * it;
+        L->pairs += n * (n - 1.0) * it;
+    }
+    return BL_OK;
+}
+
 // Runs `iters` iterations of every layout in Ls (exact mode, minibatch BS).
-// Graphs that fit the batched kernel go into one persistent launch per chunk of
-// iterations, the chunk launches captured once into a CUDA graph; the others run
-// through the whole-GPU engine one at a time afterwards.
+// Graphs that fit the batched kernel share its launches; a graph whose work is
+// above one SM's fair share (and any graph above the kernel's limits) runs on the
+// whole-GPU engine afterwards, one at a time.
 bl_status batch_run(bl_layout* const* Ls, int count, int iters, int BS, int chunk, cudaStream_t st,
                     double* elapsed_ms) {
     if (count == 0 || iters == 0) return BL_OK;
@@ -390,112 +500,22 @@ bl_status batch_run(bl_layout* const* Ls, int count, int iters, int BS, int chun
         const double n = Ls[k]->g->n;
         total += n * n;
     }
-    std::vector<int> small, big;
+    std::vector<BatchJob> small;
+    std::vector<bl_layout*> big;
     for (int k = 0; k < count; k++) {
         const int n = Ls[k]->g->n;
         const double w = (double)n * n;
-        // a graph whose work exceeds an SM's fair share would finish last on one SM
         const bool fits = n <= kBatchMaxN && BS <= kBatchMaxBS && (w <= total / sms || n <= 2048);
-        (fits ? small : big).push_back(k);
+        if (fits) small.push_back(BatchJob{Ls[k], iters, BS});
+        else big.push_back(Ls[k]);
     }
-    std::sort(small.begin(), small.end(), [&](int a, int b) {
-        return Ls[a]->g->n != Ls[b]->g->n ? Ls[a]->g->n > Ls[b]->g->n : a < b;
-    });
     cudaEvent_t e0, e1;
     BL_CUDA_TRY(cudaEventCreate(&e0));
     BL_CUDA_TRY(cudaEventCreate(&e1));
     BL_CUDA_TRY(cudaEventRecord(e0, st));
-    bl_status s = BL_OK;
-    if (!small.empty()) {
-        const Allocator al = current_allocator();
-        int ncap = 1;
-        for (int k : small) ncap = std::max(ncap, Ls[k]->g->n);
-        ncap = std::min((ncap + 63) / 64 * 64, kBatchMaxN);
-        if (chunk <= 0 || chunk > iters) chunk = iters;
-        const int nchunks = (iters + chunk - 1) / chunk;
-        const int ns = (int)small.size();
-        std::vector<BatchItem> items((size_t)nchunks * ns);
-        for (int j = 0; j < ns && s == BL_OK; j++) {
-            bl_layout* L = Ls[small[j]];
-            s = L->energy.ensure(L->alloc, (size_t)iters * sizeof(double));
-            double step = 1.0;
-            for (int64_t q = 0; q < L->t; q++) step *= 0.999;
-            for (int c = 0; c < nchunks; c++) {
-                BatchItem& it = items[(size_t)c * ns + j];
-                it.rowptr = L->g->rowptr.as<int>();
-                it.colids = L->g->colids.as<int>();
-                it.pos = L->pos.as<float2>();
-                it.energy = L->energy.as<double>() + (size_t)c * chunk;
-                it.step0 = step;
-                it.n = L->g->n;
-                it.BS = BS;
-                it.iters = std::min(chunk, iters - c * chunk);
-                it.rn = L->prm.repulse_neighbors;
-                it.invK = 1.0f / L->prm.K;
-                it.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
-                for (int q = 0; q < it.iters; q++) step *= 0.999;
-            }
-        }
-        int shape = 0;
-        if (s == BL_OK) {
-            std::vector<BatchItem> first(items.begin(), items.begin() + ns);
-            s = autotune(ncap, first, al, st, &shape);
-        }
-        DevBuf ditems, dnext;
-        if (s == BL_OK) s = ditems.ensure(al, items.size() * sizeof(BatchItem));
-        if (s == BL_OK) s = dnext.ensure(al, (size_t)nchunks * 16);
-        if (s == BL_OK) {
-            cudaError_t e = cudaMemcpyAsync(ditems.p, items.data(), items.size() * sizeof(BatchItem),
-                                            cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) s = cuda_error(e, "batched layout: work list upload");
-        }
-        if (s == BL_OK) {
-            // one persistent launch per chunk of iterations, captured into a CUDA graph
-            int grid = 0;
-            s = shape_grid(shape, ncap, ns, &grid);
-            cudaStream_t cs = nullptr;
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            if (s == BL_OK) {
-                cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-                if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-                for (int c = 0; c < nchunks && e == cudaSuccess; c++) {
-                    unsigned* next = reinterpret_cast<unsigned*>(static_cast<char*>(dnext.p) + 16 * c);
-                    e = cudaMemsetAsync(next, 0, sizeof(unsigned), cs);
-                    BatchArgs args{ditems.as<BatchItem>() + (size_t)c * ns, ns, next, ncap};
-                    void* kargs[] = {&args};
-                    if (e == cudaSuccess)
-                        e = cudaLaunchKernel(kShapes[shape].fn, dim3(grid), dim3(kShapes[shape].T), kargs,
-                                             batch_smem_bytes(ncap), cs);
-                }
-                if (cs) {
-                    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-                if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-                if (e != cudaSuccess) s = cuda_error(e, "batched layout: graph launch");
-                if (exec) cudaGraphExecDestroy(exec);
-                if (graph) cudaGraphDestroy(graph);
-                if (cs) cudaStreamDestroy(cs);
-            }
-        }
-        ditems.release();
-        dnext.release();
-        if (s == BL_OK) {
-            for (int k : small) {
-                bl_layout* L = Ls[k];
-                const double n = (double)L->g->n;
-                L->last_iters = iters;
-                L->t += iters;
-                L->vupd += n * iters;
-                L->pairs += n * (n - 1.0) * iters;
-            }
-        }
-    }
+    bl_status s = batch_launch(small.data(), (int)small.size(), chunk, st);
     for (size_t q = 0; q < big.size() && s == BL_OK; q++) {
-        bl_layout* L = Ls[big[q]];
+        bl_layout* L = big[q];
         s = exact_run(L, iters, BS, false, nullptr, st);
         if (s == BL_OK) {
             const double n = (double)L->g->n;
@@ -558,7 +578,7 @@ extern "C" bl_status bl_layout_batch(const bl_graph* const* gs, int32_t count, c
     size_t off = 0;
     for (int k = 0; k < count && s == BL_OK; k++) {
         seeded_positions(gs[k]->n, seeds[k], xy.data() + off);
-        s = layout_create(gs[k], xy.data() + off, seeds[k], 0, nullptr, false, &outs[k]);
+        s = layout_create(gs[k], xy.data() + off, seeds[k], 0, nullptr, false, current_stream(), &outs[k]);
         off += 2 * (size_t)gs[k]->n;
     }
     if (s == BL_OK) {

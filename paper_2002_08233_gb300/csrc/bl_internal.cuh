@@ -162,6 +162,9 @@ unsigned* layout_barrier_word(bl_layout* L);
 // Per-iteration energies: energy[t] = sum over CTAs of e_iter[t][cta], in order.
 bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, cudaStream_t st);
 
+// Barnes-Hut iterations of one layout (bl_bh.cu); the caller updates L's counters.
+bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st);
+
 // Whole-GPU exact run of one layout (bl_runtime.cu); the caller updates L's counters.
 bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_out, cudaStream_t st);
 
@@ -172,7 +175,7 @@ void seeded_positions(int32_t n, uint64_t seed, float* xy);
 // without waiting for the upload (bl_runtime.cu). xy must stay valid until the
 // stream reaches the copy.
 bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
-                        const bl_force_params* params, bool sync, bl_layout** out);
+                        const bl_force_params* params, bool sync, cudaStream_t st, bl_layout** out);
 
 // ---------------------------------------------------------------------------
 // batched engine (bl_batch.cu)
@@ -186,6 +189,17 @@ constexpr int kBatchMaxBS = 256;    // largest minibatch of the batched kernel
 // through exact_run one at a time. Updates the layouts' counters; synchronises.
 bl_status batch_run(bl_layout* const* Ls, int count, int iters, int BS, int chunk, cudaStream_t st,
                     double* elapsed_ms);
+
+// One layout's share of a batched launch.
+struct BatchJob {
+    bl_layout* L;
+    int iters;
+    int BS;   // <= kBatchMaxBS
+};
+// Runs every job (each must satisfy n <= kBatchMaxN) in persistent launches of at
+// most `chunk` iterations (chunk <= 0: one launch), captured into one CUDA graph.
+// Updates the layouts' counters; synchronises.
+bl_status batch_launch(const BatchJob* jobs, int count, int chunk, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // helpers

@@ -191,7 +191,7 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
 
 namespace bl {
 bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
-                        const bl_force_params* params, bool sync, bl_layout** out) {
+                        const bl_force_params* params, bool sync, cudaStream_t st, bl_layout** out) {
     if (!out) return set_error(BL_EINVAL, "bl_layout_init: out is NULL");
     *out = nullptr;
     if (!g) return set_error(BL_EINVAL, "bl_layout_init: NULL graph");
@@ -215,7 +215,6 @@ bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64
             seeded_positions(g->n, seed, h.data());
             src = h.data();
         }
-        cudaStream_t st = current_stream();
         cudaError_t e = cudaMemcpyAsync(L->pos.p, src, (size_t)g->n * sizeof(float2),
                                         cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(L->status.p, 0, kStatusBytes, st);
@@ -356,7 +355,7 @@ void bl_graph_free(bl_graph* g) {
 
 bl_status bl_layout_init(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
                          const bl_force_params* params, bl_layout** out) {
-    return layout_create(g, xy, seed, start_iter, params, true, out);
+    return layout_create(g, xy, seed, start_iter, params, true, current_stream(), out);
 }
 
 
