@@ -211,8 +211,9 @@ bl_status bl_layout_run_batch(bl_layout *const *Ls, int32_t count, int32_t iters
  * (positions, energies, Barnes-Hut trees; the graphs themselves belong to the
  * caller). Each tick the worker admits queued requests in arrival order while
  * they fit the budget (whole-GPU jobs also need one of 4 slots), then advances
- * every admitted request: exact requests of at most 16,384 vertices and batch
- * <= 256 share one persistent batched launch (50 iterations per tick); the
+ * every admitted request: exact requests of at most 16,384 vertices, batch
+ * <= 256 and n^2 x iters <= 2.5e9 share one persistent batched launch (50
+ * iterations per tick); the
  * others (larger exact, and BH) run a chunk whose length depends only on the
  * request. A finished layout is copied to host memory and its device memory
  * returns to the budget at once. A request's result does not depend on what

@@ -4,8 +4,8 @@
 // requests in arrival order while their working memory fits the budget (and,
 // for jobs that need the whole GPU, while a slot is free), then advances every
 // admitted job by one chunk of iterations:
-//   - exact jobs of at most 16,384 vertices share one persistent batched launch
-//     (one CTA per graph, 50 iterations per tick);
+//   - exact jobs of at most 16,384 vertices and n^2 x iterations <= 2.5e9 share
+//     one persistent batched launch (one CTA per graph, 50 iterations per tick);
 //   - larger exact jobs and Barnes-Hut jobs take the whole GPU for a chunk whose
 //     length depends only on the job's size and mode (about 25 ms of work).
 // Jobs that finish are copied to host memory and their device memory returns to
@@ -41,6 +41,7 @@ constexpr int kSmallChunk = 50;          // iterations per tick of a batched job
 constexpr int kBigSlots = 4;             // whole-GPU jobs admitted at a time
 constexpr double kBigChunkMs = 25.0;     // target work per whole-GPU chunk
 constexpr int kAutoExactBelow = 50000;   // BL_AUTO: exact below this many vertices
+constexpr double kBatchedWorkMax = 2.5e9; // n^2 x iterations of a job the batched launch takes
 
 enum class JobState { Queued, Active, Done, Failed, Canceled };
 
@@ -265,7 +266,10 @@ bl_status bl_serve_submit(bl_server* S, const bl_graph* g, uint64_t seed, int32_
     j->BS = batch;
     j->mode = mode;
     j->theta = theta;
-    j->small = mode == BL_EXACT && g->n <= kBatchMaxN && batch <= kBatchMaxBS;
+    // one CTA holds a batched job for all its iterations: above about 0.1 s of one
+    // SM's work, the whole GPU finishes the job sooner
+    j->small = mode == BL_EXACT && g->n <= kBatchMaxN && batch <= kBatchMaxBS &&
+               (double)g->n * g->n * iters <= kBatchedWorkMax;
     j->chunk = j->small ? kSmallChunk : big_chunk(*j);
     j->bytes = job_bytes(*j);
     if (j->bytes > S->budget) {

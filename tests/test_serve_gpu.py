@@ -109,24 +109,25 @@ def test_admission_under_a_tight_budget(core):
 
 
 def test_cancel(core):
+    """Four whole-GPU requests fill the server's whole-GPU slots, so a fifth one
+    queues: it can be canceled, a running one cannot."""
     g = synth.erdos_renyi(3000, 5.0, 5)
-    budget = 8 * 3000 + 8 * 3000 + 4096 + 10
-    S = core.Server(budget)
+    S = core.Server(GB)
     G = core.Graph(g)
-    t1 = S.submit(G, 1, 3000, 64, "exact")   # holds the whole budget for a while
-    t2 = S.submit(G, 2, 3000, 64, "exact")
+    running = [S.submit(G, k, 3000, 64, "exact") for k in range(4)]
+    queued = S.submit(G, 9, 3000, 64, "exact")
     t0 = time.time()
-    while S.stats()["in_flight"] < 1:
+    while S.stats()["in_flight"] < 4:
         assert time.time() - t0 < 30
         time.sleep(0.001)
-    S.cancel(t2)
+    S.cancel(queued)
     with pytest.raises(core.BatchLayoutError) as e:
-        S.cancel(t1)
+        S.cancel(running[0])
     assert e.value.status == core.BL_EBUSY
     with pytest.raises(core.BatchLayoutError) as e:
-        S.poll(t2, g.n)
+        S.poll(queued, g.n)
     assert e.value.status == core.BL_ECANCELED
-    S.close()   # drops the running request
+    S.close()   # drops the running requests
 
 
 def test_zero_iterations_and_poll_errors(core):
