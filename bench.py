@@ -44,6 +44,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-also", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None,
+                    choices=["bh_rmat20", "grid32_600it", "batched_4096", "serving"],
+                    help="run one secondary workload alone and print its line (profiling)")
+    ap.add_argument("--batched-count", type=int, default=4096, help="graphs of the batched line")
+    ap.add_argument("--batched-iters", type=int, default=300, help="iterations of the batched line")
+    ap.add_argument("--bh-scale", type=int, default=20, help="R-MAT scale of the BH line")
+    ap.add_argument("--serve-count", type=int, default=32, help="requests of the serving line")
     return ap.parse_args()
 
 
@@ -336,7 +343,8 @@ def run_bh(args, local, steps=5, warmup=2):
     from paper_2002_08233_gb300 import core, synth
     core.load()
     stream = core.use_torch()
-    g = synth.rmat_scale20()
+    g = synth.rmat_scale20() if args.bh_scale == 20 else synth.rmat(args.bh_scale, 16, 0.57, 0.19,
+                                                                      0.19, seed=3)
     n = g.n
     G = core.Graph(g)
     L = core.Layout(G, seed=0)
@@ -353,8 +361,8 @@ def run_bh(args, local, steps=5, warmup=2):
     st = L.stats()
     total = sum(ms)
     return {
-        "workload": "Barnes-Hut BatchLayout, R-MAT scale 20 (n=1,048,576, edge factor 16, "
-                    "a=.57 b=c=.19), minibatch 256, theta 1.2, one iteration per step",
+        "workload": f"Barnes-Hut BatchLayout, R-MAT scale {args.bh_scale} (n={n:,}, edge factor "
+                    "16, a=.57 b=c=.19), minibatch 256, theta 1.2, one iteration per step",
         "metric": "vertex-updates/s", "value": n * steps / (total / 1e3),
         "ms_per_iteration": total / steps, "steps": steps, "warmup": warmup,
         "n": n, "nnz": g.nnz,
@@ -408,10 +416,10 @@ def run_batched(args, local):
     from paper_2002_08233_gb300 import core, synth
     core.load()
     core.use_torch()
-    gs = synth.small_graph_mix(count=4096, seed=4)
+    gs = synth.small_graph_mix(count=args.batched_count, seed=4)
     Gs = [core.Graph(g) for g in gs]
     seeds = np.arange(len(gs), dtype=np.uint64)
-    iters, bs = 300, 64
+    iters, bs = args.batched_iters, 64
     pairs = float(sum(g.n * (g.n - 1) for g in gs)) * iters
     # resident inputs: layouts created, then one timed batched run
     Ls = core.layout_batch(Gs, seeds, 0, bs)
@@ -439,14 +447,14 @@ def run_batched(args, local):
     e2e_s = time.perf_counter() - t0
     n_tot = sum(g.n for g in gs)
     # one graph per launch (the whole-GPU engine), on an even sample of 128 graphs
-    idx = np.linspace(0, len(gs) - 1, 128).astype(int)
+    idx = np.linspace(0, len(gs) - 1, min(128, len(gs))).astype(int)
     plain_ms = 0.0
     for k in idx:
         L = core.Layout(Gs[k], seed=int(seeds[k]))
-        L.run(30, bs, "exact")
+        L.run(min(30, iters), bs, "exact")
         plain_ms += L.stats()["last_run_ms"]
         L.close()
-    plain_s = plain_ms / 1e3 * (len(gs) / len(idx)) * (iters / 30)
+    plain_s = plain_ms / 1e3 * (len(gs) / len(idx)) * (iters / min(30, iters))
     # stress at the same seeds: batched vs one graph per launch, 16 graphs
     sp, sb = [], []
     for k in idx[::2]:
@@ -458,9 +466,9 @@ def run_batched(args, local):
     sp, sb = np.array(sp), np.array(sb)
     ratio = sb / sp - 1.0
     return {
-        "workload": "4,096 graphs, n log-uniform [50, 5,000] (grids, random binary trees, ER mean "
-                    "degree U[4,8]; seed 4), exact, minibatch 64, 300 iterations, one persistent "
-                    "launch (CUDA-graph captured)",
+        "workload": f"{len(gs):,} graphs, n log-uniform [50, 5,000] (grids, random binary trees, "
+                    f"ER mean degree U[4,8]; seed 4), exact, minibatch 64, {iters} iterations, one "
+                    "persistent launch (CUDA-graph captured)",
         "metric": "pair-interactions/s", "value": pairs / t, "layouts_per_s": len(gs) / t,
         "seconds": t, "graphs": len(gs), "vertices": n_tot,
         "roofline": {"bound": "alu", "achieved": pairs / t / 1e9, "peak": peak_pairs / 1e9,
@@ -469,8 +477,8 @@ def run_batched(args, local):
         "e2e": {"value": pairs / e2e_s, "unit": "pair-interactions/s", "layouts_per_s": len(gs) / e2e_s,
                 "h2d_bytes_per_step": int(8 * n_tot), "d2h_bytes_per_step": int(8 * n_tot)},
         "one_graph_per_launch": {"layouts_per_s": len(gs) / plain_s,
-                                 "sample": "128 evenly spaced graphs x 30 iterations, scaled to "
-                                           "4,096 x 300"},
+                                 "sample": f"{len(idx)} evenly spaced graphs x {min(30, iters)} "
+                                           f"iterations, scaled to {len(gs)} x {iters}"},
         "speedup_vs_one_graph_per_launch": plain_s / t,
         # per graph the two FP32 trajectories may settle in different local minima
         # (grids, trees); the ensemble is what must agree
@@ -485,7 +493,8 @@ def run_batched(args, local):
 # secondary: the serving loop
 # ---------------------------------------------------------------------------
 
-def run_serving(args, local, count=32):
+def run_serving(args, local):
+    count = args.serve_count
     import numpy as np
     import torch
 
@@ -543,6 +552,13 @@ def main():
         out = run_reference(args, rank, world)
         if rank == 0 and out is not None:
             print(json.dumps(out))
+        return
+    if args.only:
+        fn = {"bh_rmat20": run_bh, "grid32_600it": run_grid, "batched_4096": run_batched,
+              "serving": run_serving}[args.only]
+        line = fn(args, local)
+        if rank == 0:
+            print(json.dumps({"only": args.only, **line}))
         return
     out, g = run_exact(args, rank, world, local)
     if not args.no_also:

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -66,7 +67,7 @@ struct BHState {
     DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
     DevBuf walkcnt;                     // unsigned long long[2]: far nodes, near pairs
     // sweep
-    int plan_bs = -1, nlevels = 0, nbig = 0;
+    int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, lvl0_rows = 0;
     DevBuf split, bigrows, old;         // row split points, rows with many old edges, old attraction
     DevBuf lvl_ptr, tasks, seg_off, seg_sum, seg_cnt;   // level-set schedule
     DevBuf e_row, epart;                // per-row |ct|^2, reduction partials
@@ -675,16 +676,17 @@ struct SweepArgs {
     unsigned* bar;
     int* status;
     int nlevels;
+    int first_level;         // levels before it are done by level0_kernel
     float invK, negRK2, stepf;
     unsigned long long* trace;   // optional: start time of each level (CTA 0)
 };
 
-constexpr int kSegEdges = 1024;   // earlier-minibatch edges per task
+constexpr int kSegEdges = 128;   // earlier-minibatch edges per task (4 gathers per lane)
 
-__device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float sx, float sy) {
-    const float2 me = a.bold[i];
-    const float2 rp = a.rep[i];
-    const float2 od = a.old[i];
+// The row's update: ct = attraction (this iteration's moved neighbours sx,sy +
+// the not-yet-moved ones od) + repulsion rp scaled by -RK^2; me = start position.
+__device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float2 me, float2 rp, float2 od,
+                                           float sx, float sy) {
     const float fx = fmaf(a.negRK2, rp.x, sx + od.x);
     const float fy = fmaf(a.negRK2, rp.y, sy + od.y);
     float nx = me.x, ny = me.y, gx = fx, gy = fy;
@@ -703,52 +705,116 @@ __device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float sx, 
     a.e_row[i] = (double)fmaf(fx, fx, fy * fy);
 }
 
+// Everything a task needs that the sweep does not change: the task record, the
+// row's start position, repulsion and not-yet-moved attraction, and the column
+// ids of its first 128 edges (4 per lane). Loaded for the next level before a
+// warp enters the level barrier, so that after it only the moved neighbours'
+// positions remain to be read.
+struct TaskPre {
+    int4 tk;
+    float2 me, rp, od;
+    int j[4];
+};
+
+__device__ __forceinline__ void task_prefetch(const SweepArgs& a, int t, int lane, TaskPre& p) {
+    p.tk = a.tasks[t];
+    const int i = p.tk.x;
+    p.me = a.bold[i];
+    p.rp = a.rep[i];
+    p.od = a.old[i];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int e = p.tk.y + lane + 32 * k;
+        p.j[k] = e < p.tk.z ? __ldg(&a.colids[e]) : -1;
+    }
+}
+
+__device__ __forceinline__ void task_run(const SweepArgs& a, const TaskPre& p, int lane) {
+    const int i = p.tk.x;
+    const int seg = p.tk.w & 0xFFFF, nseg = p.tk.w >> 16;
+    const float2 me = p.me;
+    float sx = 0.f, sy = 0.f;
+    {   // first 128 edges: ids already in registers
+        float2 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) q[k] = p.j[k] >= 0 ? __ldcg(&a.bnew[p.j[k]]) : me;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (p.j[k] >= 0) attr_term(me, q[k], a.invK, sx, sy);
+    }
+    for (int e = p.tk.y + 128 + lane; e < p.tk.z; e += 128) {   // 4 gathers in flight per lane
+        int j[4];
+        float2 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) j[k] = e + 32 * k < p.tk.z ? __ldg(&a.colids[e + 32 * k]) : -1;
+#pragma unroll
+        for (int k = 0; k < 4; k++) q[k] = j[k] >= 0 ? __ldcg(&a.bnew[j[k]]) : me;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (j[k] >= 0) attr_term(me, q[k], a.invK, sx, sy);
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) {
+        if (nseg <= 1) {
+            finish_row(a, i, me, p.rp, p.od, sx, sy);
+        } else {
+            const int off = a.seg_off[i];
+            a.seg_sum[off + seg] = make_float2(sx, sy);
+            __threadfence();
+            if (atomicAdd(&a.seg_cnt[i], 1) == nseg - 1) {
+                __threadfence();
+                float tx = 0.f, ty = 0.f;
+                for (int q = 0; q < nseg; q++) {   // segments in order
+                    const float2 v = __ldcg(&a.seg_sum[off + q]);
+                    tx += v.x;
+                    ty += v.y;
+                }
+                finish_row(a, i, me, p.rp, p.od, tx, ty);
+            }
+        }
+    }
+}
+
+// The first level: rows with no neighbour in an earlier minibatch. Nothing they
+// read moves during the sweep, so they need no barrier: one thread per row.
+__global__ void level0_kernel(SweepArgs a) {
+    const int t1 = a.lvl_ptr[1];
+    for (int t = a.lvl_ptr[0] + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
+        const int i = a.tasks[t].x;
+        finish_row(a, i, a.bold[i], a.rep[i], a.old[i], 0.f, 0.f);
+    }
+}
+
 __global__ void __launch_bounds__(kSweepThreads) level_sweep_kernel(SweepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     GridBarrier bar{a.bar, a.status, gridDim.x, 0u};
-    for (int l = 0; l < a.nlevels; l++) {
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0)
+        for (int q = 0; q < a.first_level && q < a.nlevels; q++) a.trace[q] = global_ns();
+    TaskPre cur;
+    const int l0 = a.first_level;
+    bool have = l0 < a.nlevels && a.lvl_ptr[l0] + gw < a.lvl_ptr[l0 + 1];
+    if (have) task_prefetch(a, a.lvl_ptr[l0] + gw, lane, cur);
+    for (int l = l0; l < a.nlevels; l++) {
         if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[l] = global_ns();
-        for (int t = a.lvl_ptr[l] + gw; t < a.lvl_ptr[l + 1]; t += nw) {
-            const int4 tk = a.tasks[t];
-            const int i = tk.x;
-            const int seg = tk.w & 0xFFFF, nseg = tk.w >> 16;
-            const float2 me = a.bold[i];
-            float sx = 0.f, sy = 0.f;
-            for (int e = tk.y + lane; e < tk.z; e += 128) {   // 4 gathers in flight per lane
-                int j[4];
-                float2 p[4];
-#pragma unroll
-                for (int k = 0; k < 4; k++) j[k] = e + 32 * k < tk.z ? __ldg(&a.colids[e + 32 * k]) : -1;
-#pragma unroll
-                for (int k = 0; k < 4; k++) p[k] = j[k] >= 0 ? __ldcg(&a.bnew[j[k]]) : me;
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (j[k] >= 0) attr_term(me, p[k], a.invK, sx, sy);
-            }
-            sx = warp_sum(sx);
-            sy = warp_sum(sy);
-            if (lane == 0) {
-                if (nseg <= 1) {
-                    finish_row(a, i, sx, sy);
-                } else {
-                    const int off = a.seg_off[i];
-                    a.seg_sum[off + seg] = make_float2(sx, sy);
-                    __threadfence();
-                    if (atomicAdd(&a.seg_cnt[i], 1) == nseg - 1) {
-                        __threadfence();
-                        float tx = 0.f, ty = 0.f;
-                        for (int q = 0; q < nseg; q++) {   // segments in order
-                            const float2 v = __ldcg(&a.seg_sum[off + q]);
-                            tx += v.x;
-                            ty += v.y;
-                        }
-                        finish_row(a, i, tx, ty);
-                    }
-                }
+        const int t0 = a.lvl_ptr[l] + gw, t1 = a.lvl_ptr[l + 1];
+        if (have) task_run(a, cur, lane);
+        if (t0 + nw < t1) {   // further tasks of this level: the next one loads while one runs
+            TaskPre p;
+            task_prefetch(a, t0 + nw, lane, p);
+            for (int t = t0 + nw; t < t1; t += nw) {
+                TaskPre q;
+                const bool more = t + nw < t1;
+                if (more) task_prefetch(a, t + nw, lane, q);
+                task_run(a, p, lane);
+                if (more) p = q;
             }
         }
+        // the next level's first task, loaded while this warp waits at the barrier
+        have = l + 1 < a.nlevels && a.lvl_ptr[l + 1] + gw < a.lvl_ptr[l + 2];
+        if (have) task_prefetch(a, a.lvl_ptr[l + 1] + gw, lane, cur);
         if (!bar.sync()) return;
     }
     if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[a.nlevels] = global_ns();
@@ -881,9 +947,18 @@ static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaSt
 // Per (graph, minibatch size): the split point of every row (first edge into its
 // own or a later minibatch), the rows with many such edges, the level of every
 // row and the sweep's tasks grouped by level.
-static bl_status bh_plan(bl_layout* L, int BS) {
+// Earlier-minibatch edges per sweep task (rows with more are cut into segments);
+// BL_BH_SEG overrides it.
+static int seg_edges() {
+    const char* e = std::getenv("BL_BH_SEG");
+    const int v = e ? std::atoi(e) : 0;
+    return v >= 32 ? v : kSegEdges;
+}
+
+static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     BHState* s = L->bh;
-    if (s->plan_bs == BS) return BL_OK;
+    const int segE = seg_edges();
+    if (s->plan_bs == BS && s->plan_seg == segE) return BL_OK;
     const bl_graph* g = L->g;
     const int n = g->n;
     const int* rp = g->h_rowptr.data();
@@ -905,7 +980,7 @@ static bl_status bh_plan(bl_layout* L, int BS) {
     std::vector<int> nseg(n);
     for (int i = 0; i < n; i++) {
         const int nd = split[i] - rp[i];
-        nseg[i] = std::max(1, div_up(nd, kSegEdges));
+        nseg[i] = std::max(1, div_up(nd, segE));
         lcount[level[i]] += nseg[i];
     }
     std::vector<int> lvl_ptr(nlev + 1, 0);   // levels 1..nlev -> slots 0..nlev-1
@@ -929,7 +1004,6 @@ static bl_status bh_plan(bl_layout* L, int BS) {
         if (ns >= 65536) return set_error(BL_EINVAL, "Barnes-Hut sweep: row too long");
     }
     const Allocator& al = L->alloc;
-    cudaStream_t st = current_stream();
     auto up = [&](DevBuf& d, const void* h, size_t bytes) -> bl_status {
         BL_TRY(d.ensure(al, std::max<size_t>(bytes, 16)));
         if (bytes) BL_CUDA_TRY(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, st));
@@ -949,12 +1023,14 @@ static bl_status bh_plan(bl_layout* L, int BS) {
     s->nbig = (int)bigrows.size();
     s->nlevels = nlev;
     s->plan_bs = BS;
+    s->plan_seg = segE;
+    s->lvl0_rows = nlev > 0 ? lvl_ptr[1] : 0;
     return BL_OK;
 }
 
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) {
     BL_TRY(bh_ensure(L));
-    BL_TRY(bh_plan(L, BS));
+    BL_TRY(bh_plan(L, BS, st));
     BHState* s = L->bh;
     const int n = L->g->n;
     BL_TRY(L->pos2.ensure(L->alloc, (size_t)n * sizeof(float2)));
@@ -963,7 +1039,9 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
     for (int64_t k = 0; k < L->t; k++) step *= 0.999;
     int occ = 0;
     BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_sweep_kernel, kSweepThreads, 0));
-    const int G = std::max(1, std::min(occ, 4)) * device_sm_count();
+    int per_sm = 2;   // sweep CTAs per SM (measured best on R-MAT 20); BL_BH_SWEEP_CTAS overrides it
+    if (const char* e = std::getenv("BL_BH_SWEEP_CTAS")) per_sm = std::max(1, std::atoi(e));
+    const int G = std::max(1, std::min(occ, per_sm)) * device_sm_count();
     const int nep = std::min(1024, div_up(n, 1024));
     for (int t = 0; t < iters; t++) {
         const float2* S = L->pos.as<float2>();
@@ -1006,6 +1084,11 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
             BL_CUDA_TRY(cudaMemsetAsync(L->trace.p, 0, tb, st));
             a.trace = L->trace.as<unsigned long long>();
             L->trace_count = s->nlevels + 1;
+        }
+        a.first_level = s->nlevels > 0 ? 1 : 0;
+        if (a.first_level == 1) {
+            const int n0 = s->lvl0_rows;
+            level0_kernel<<<std::max(1, std::min(div_up(n0, 256), 8 * device_sm_count())), 256, 0, st>>>(a);
         }
         void* args[] = {&a};
         BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)level_sweep_kernel, dim3(G),
