@@ -80,6 +80,12 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+def whole_job_rate(units_per_rank, seconds, world):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's
+    time (every rank times the same amount of work)."""
+    return units_per_rank * world / max_over_ranks(seconds, world)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -193,7 +199,7 @@ def run_exact(args, rank, world, local):
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), world)
-    value = pairs_per_iter * ITERS_PER_STEP * args.steps * world / (total_ms / 1e3)
+    value = whole_job_rate(pairs_per_iter * ITERS_PER_STEP * args.steps, total_ms / 1e3, world)
 
     # end to end through the public API with pinned host buffers
     host_in = torch.from_numpy(x0.copy()).pin_memory()

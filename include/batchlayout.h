@@ -272,6 +272,14 @@ bl_status bl_layout_run_noalloc(int32_t n, const int32_t *d_rowptr, const int32_
                                 const bl_force_params *params, int64_t start_iter,
                                 double *d_energy, void *stream);
 
+/* ---- failure-detection hook --------------------------------------------------- */
+
+/* Test hook (the paper has no counterpart): runs the engines' bounded grid
+ * barrier in a 2-CTA cooperative kernel that expects 3 CTAs, so the barrier can
+ * never complete; each wait gives up after limit_ms (1..2000) and the call
+ * returns BL_ETIMEOUT with the context still usable. Synchronises. */
+bl_status bl_debug_barrier_timeout(int32_t limit_ms);
+
 /* ---- parity hooks ------------------------------------------------------------ */
 
 /* One-snapshot forces ct_i (FP32, 2 floats per vertex) for i in [lo, hi) from

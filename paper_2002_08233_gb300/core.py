@@ -85,6 +85,7 @@ def _declare(lib):
         "bl_get_trace": [P, P, i64, P],
         "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
         "bl_layout_run_batch": [P, i32, i32, i32],
+        "bl_debug_barrier_timeout": [i32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name, None)

@@ -287,6 +287,7 @@ struct GridBarrier {
     int* status;
     unsigned nblocks;
     unsigned phase;
+    unsigned long long limit_ns = kWaitLimitNs;   // give up (BL_ETIMEOUT) after this long
     __device__ bool sync() {
         __syncthreads();
         __shared__ int s_ok;
@@ -302,7 +303,7 @@ struct GridBarrier {
                 if ((int)(v - target) >= 0) break;
                 if ((spin & 255u) == 255u) {
                     if (ld_volatile_i32(status) != 0) { ok = 0; break; }
-                    if (global_ns() - t0 > kWaitLimitNs) {
+                    if (global_ns() - t0 > limit_ns) {
                         atomicCAS(status, 0, (int)BL_ETIMEOUT);
                         ok = 0;
                         break;
