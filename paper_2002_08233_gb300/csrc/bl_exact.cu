@@ -74,7 +74,7 @@ __device__ __forceinline__ void tile_pairs2(const float4* __restrict__ tile, int
         asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(AY[m]) : "l"(dy), "l"(inv));
     };
     if (mlo == 0 && mhi == RPT) {   // every row: no predicate in the loop
-#pragma unroll 4
+#pragma unroll 8
         for (int q = 0; q < np; q++) {
             const float4 p = tile[q];
             const f32x2 X = pk2(p.x, p.y), Y = pk2(p.z, p.w);
@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     //      share few minibatches and whole warps skip columns they do not need);
     //      blocks go first to the warps that do not share a sub-partition with the
     //      control warp (hardware warp w runs on sub-partition w % 4) -------------------
-    const int wslot = (wb + 1) % 4 == 0 ? (NW / 4) * 3 + wb / 4
-                                         : ((wb + 1) % 4 - 1) + 3 * (wb / 4);
+    const int wslot = (wb + 1) % 4 == 0 ? (NW - NW / 4) + (wb + 1) / 4 - 1
+                                         : wb - (wb + 1) / 4;
     f32x2 XI[RPT], YI[RPT];
     float sx[RPT], sy[RPT], cx[RPT], cy[RPT];
     int bi[RPT], lrow[RPT];
@@ -382,17 +382,20 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         for (int c0 = 0; c0 < hi - lo; c0 += kCritLanes) {
             const int nr = min(kCritLanes, hi - lo - c0);
             // column kprev: lane group g = lane / 8 takes row c0 + g
-            const int g = lane >> 3, gl = lane & 7;
+            // W lanes per row: the whole warp shares the column tile among the rows
+            const int lw = nr == 1 ? 5 : (nr == 2 ? 4 : 3);
+            const int W = 1 << lw;
+            const int g = lane >> lw, gl = lane & (W - 1);
             float rx = 0.f, ry = 0.f;
-            if (g < nr) {
+            if (g < nr) {   // unrolled: the loads and reciprocals of 8 columns overlap
                 const float2 me = s_pos[lo + c0 + g];
-                for (int q = gl; q < kpn; q += 8) {
+#pragma unroll 8
+                for (int q = gl; q < kpn; q += W) {
                     const float2 pc = tile_col(tile, q);
                     rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
                 }
             }
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
+            for (int o = W >> 1; o > 0; o >>= 1) {
                 rx += __shfl_xor_sync(0xffffffffu, rx, o);
                 ry += __shfl_xor_sync(0xffffffffu, ry, o);
             }
@@ -414,19 +417,38 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     hax = ax; hay = ay; hqx = qx; hqy = qy;
                 }
             }
-            // lane r finishes row c0 + r; its column sum sits in lane group r
-            const float rxs = __shfl_sync(0xffffffffu, rx, (lane & 3) * 8);
-            const float rys = __shfl_sync(0xffffffffu, ry, (lane & 3) * 8);
-            if (lane < nr) {
-                const int c = c0 + lane;
+            // rows with at most 32 edges: the row's W lanes split its edges
+            float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
+            if (g < nr) {
+                const int li = lo + c0 + g;
+                const int e0 = s_rpl[li], e1 = s_rpe[li];
+                if (e1 - e0 <= 32) {
+                    const float2 me = s_pos[li];
+                    for (int ee = e0 + gl; ee < e1; ee += W)
+                        edge_terms(me.x, me.y, nbr_pos(c0 + g, ee, e0), invK, rn, ax, ay, qx, qy);
+                }
+            }
+            for (int o = W >> 1; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                qx += __shfl_xor_sync(0xffffffffu, qx, o);
+                qy += __shfl_xor_sync(0xffffffffu, qy, o);
+            }
+            // the first lane of group g finishes row c0 + g (hub sums sit in lane g)
+            const float hax_g = __shfl_sync(0xffffffffu, hax, g & 31);
+            const float hay_g = __shfl_sync(0xffffffffu, hay, g & 31);
+            const float hqx_g = __shfl_sync(0xffffffffu, hqx, g & 31);
+            const float hqy_g = __shfl_sync(0xffffffffu, hqy, g & 31);
+            const float rxs = rx, rys = ry;
+            if (gl == 0 && g < nr) {
+                const int c = c0 + g;
                 const int li = lo + c;
                 const int i = rank + G * li;
                 const float2 me = s_pos[li];
                 const int e0 = s_rpl[li], e1 = s_rpe[li];
-                float ax = hax, ay = hay, qx = hqx, qy = hqy;
-                if (e1 - e0 <= 32)
-                    for (int ee = e0; ee < e1; ee++)
-                        edge_terms(me.x, me.y, nbr_pos(c, ee, e0), invK, rn, ax, ay, qx, qy);
+                if (e1 - e0 > 32) {
+                    ax = hax_g; ay = hay_g; qx = hqx_g; qy = hqy_g;
+                }
                 float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
                 if (kprev >= 0) {
                     kahan_add(sxr, cxr, rxs);
@@ -535,7 +557,26 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 }
                 // the buffer batch kprev was written to at step s-1
                 const float2* bprev = (k == 0) ? bold : bnew;
-                copy_tile(tile, bprev + (size_t)kprev * BS, min(BS, n - kprev * BS), lane, 32);
+                {   // the control warp copies the tile; each lane issues 4 column pairs'
+                    // loads before storing any, so the copy costs about one round trip
+                    const float2* src = bprev + (size_t)kprev * BS;
+                    const int nc = min(BS, n - kprev * BS);
+                    const int nq = (nc + 1) / 2;
+                    for (int q0 = 0; q0 < nq; q0 += 128) {
+                        float2 va[4], vb[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int q = q0 + lane + 32 * u;
+                            va[u] = q < nq ? __ldcg(&src[2 * q]) : make_float2(0.f, 0.f);
+                            vb[u] = (q < nq && 2 * q + 1 < nc) ? __ldcg(&src[2 * q + 1]) : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int q = q0 + lane + 32 * u;
+                            if (q < nq) tile[q] = make_float4(va[u].x, vb[u].x, va[u].y, vb[u].y);
+                        }
+                    }
+                }
                 __syncwarp();
             }
             if (lane == 0) trace_mark(tk, rank, s, 2);
@@ -664,8 +705,10 @@ static bl_status dispatch_rpt(const ExactPlan& pl, const ExactTask& tk, const Ex
 }
 
 // Launch shape: G = one CTA per SM (at least 64 rows each); bulk threads TB and
-// rows per thread by the rows per CTA: up to 512 rows one row per thread of 512,
-// up to 2048 rows 512 threads x 2..4 rows, beyond that 256 threads x 6..8 rows.
+// rows per thread by the rows per CTA: up to 512 rows one row per thread, the
+// bulk rounded up to whole warps (256, 320, 384, 448 or 512 threads) so that few
+// lanes idle in the pair loop; up to 2048 rows 512 threads x 2..4 rows, beyond
+// that 256 threads x 6..8 rows.
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out) {
     if (n <= 0 || BS <= 0) return set_error(BL_EINVAL, "exact engine: empty problem");
     const int sms = device_sm_count();
@@ -675,7 +718,18 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
     }
     const int G = ctas_hint > 0 ? ctas_hint : std::min(sms, std::max(1, div_up(n, 64)));
     const int nloc = div_up(n, G);
-    int T = threads_hint == 256 || threads_hint == 512 ? threads_hint : (nloc <= 256 ? 256 : 512);
+    const bool hint_ok = threads_hint == 256 || threads_hint == 320 || threads_hint == 384 ||
+                         threads_hint == 448 || threads_hint == 512;
+    // Default 256 or 512: a shape with fewer bulk warps leaves more rows on the
+    // sub-partition the control warp shares, which slows the per-minibatch chain
+    // (measured: 448 threads on n = 65,536 ran 6% slower than 512). The in-between
+    // shapes stay available through BL_EXACT_THREADS.
+    int T = hint_ok ? threads_hint : (nloc <= 256 ? 256 : 512);
+    if (T != 256 && T != 512 && div_up(nloc, T) > 1) T = 512;   // the in-between shapes take one row each
+    if (T == 288) T = 320;
+    if (T == 352) T = 384;
+    if (T == 416) T = 448;
+    if (T == 480) T = 512;
     int rpt = div_up(nloc, T);
     if (T == 512 && rpt > 4) {
         T = 256;
@@ -712,6 +766,9 @@ bl_status exact_launch(const ExactPlan& pl, const ExactTask& task, const ExactPa
     if (task.BS > kMaxBatch) return set_error(BL_EINVAL, "exact engine: batch too large");
     switch (pl.T) {
         case 512: return dispatch_rpt<512>(pl, task, prm, st);
+        case 448: return launch_grid_t<1, 448>(pl, task, prm, st);
+        case 384: return launch_grid_t<1, 384>(pl, task, prm, st);
+        case 320: return launch_grid_t<1, 320>(pl, task, prm, st);
         default: return dispatch_rpt<256>(pl, task, prm, st);
     }
 }

@@ -205,3 +205,22 @@ def test_ba65536_one_iteration(core, ba65k):
     _, sens = oracle_sensitivity(g, xy, 1, 256, trials=1, nthreads=NCPU)
     assert err <= position_tolerance(TOL_POS_EXACT, sens), (err, sens)
     assert L.energy_history()[0] == pytest.approx(er[0], rel=1e-4)
+
+
+@pytest.mark.parametrize("threads", ["320", "384", "448"])
+def test_bulk_shape_does_not_change_results(core, threads):
+    """Bulk warps only decide which thread holds a row, not any row's summation
+    order: every shape gives the 512-thread shape's positions bit for bit."""
+    g = synth.erdos_renyi(45000, 4.0, 12)   # 297 rows per CTA on 152 SMs
+    xy = synth.uniform_positions(g.n, 12)
+    out = {}
+    for t in ("512", threads):
+        os.environ["BL_EXACT_THREADS"] = t
+        try:
+            _, L = _layout(core, g, xy)
+            L.run(2, 256, "exact")
+            out[t] = (L.positions(), L.energy_history())
+        finally:
+            os.environ.pop("BL_EXACT_THREADS", None)
+    assert np.array_equal(out["512"][0], out[threads][0])
+    assert np.array_equal(out["512"][1], out[threads][1])
