@@ -377,22 +377,27 @@ __global__ void node_emit_kernel(const unsigned* __restrict__ codes, int n,
                                  const int* __restrict__ first_node, int* __restrict__ nd_first,
                                  int* __restrict__ nd_count, int* __restrict__ nd_level,
                                  int* __restrict__ nd_skip, int* __restrict__ lvl_cnt) {
+    __shared__ int s_cnt[kLevels + 1];   // this block's nodes per level
+    if (threadIdx.x <= kLevels) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int lmin, lmax;
-    node_levels(codes, n, k, lmin, lmax);
-    if (lmax < lmin) return;
-    const int M = first_node[n];
-    const unsigned c = codes[k];
-    int v = first_node[k];
-    for (int l = lmin; l <= lmax; l++, v++) {
-        const int e = cell_end(codes, n, k + 1, c, l);
-        nd_first[v] = k;
-        nd_count[v] = e - k;
-        nd_level[v] = l;
-        nd_skip[v] = e >= n ? M : first_node[e];
-        atomicAdd(&lvl_cnt[l], 1);
+    if (k < n) {
+        int lmin, lmax;
+        node_levels(codes, n, k, lmin, lmax);
+        const int M = first_node[n];
+        const unsigned c = codes[k];
+        int v = first_node[k];
+        for (int l = lmin; l <= lmax; l++, v++) {
+            const int e = cell_end(codes, n, k + 1, c, l);
+            nd_first[v] = k;
+            nd_count[v] = e - k;
+            nd_level[v] = l;
+            nd_skip[v] = e >= n ? M : first_node[e];
+            atomicAdd(&s_cnt[l], 1);
+        }
     }
+    __syncthreads();
+    if (threadIdx.x <= kLevels && s_cnt[threadIdx.x] > 0) atomicAdd(&lvl_cnt[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
 // lvl[0..16] counts -> lvl[20..37] offsets, lvl[40..56] fill cursors
@@ -409,10 +414,25 @@ __global__ void level_offsets_kernel(int* __restrict__ lvl) {
 
 __global__ void level_bucket_kernel(const int* __restrict__ nd_level, const int* __restrict__ first_node,
                                     int n, int* __restrict__ lvl, int* __restrict__ lvl_nodes) {
+    // each block buckets a contiguous range: count per level in shared memory,
+    // reserve each level's room with one global atomic, then scatter
+    __shared__ int s_cnt[kLevels + 1], s_base[kLevels + 1];
     const int M = first_node[n];
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M; v += gridDim.x * blockDim.x) {
-        const int slot = atomicAdd(&lvl[40 + nd_level[v]], 1);
-        lvl_nodes[slot] = v;
+    const int per = (M + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * per, hi = min(M, lo + per);
+    if (threadIdx.x <= kLevels) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) atomicAdd(&s_cnt[nd_level[v]], 1);
+    __syncthreads();
+    if (threadIdx.x <= kLevels) {
+        const int c = s_cnt[threadIdx.x];
+        s_base[threadIdx.x] = c > 0 ? atomicAdd(&lvl[40 + threadIdx.x], c) : 0;
+        s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const int l = nd_level[v];
+        lvl_nodes[s_base[l] + atomicAdd(&s_cnt[l], 1)] = v;
     }
 }
 
@@ -580,8 +600,8 @@ __global__ void bh_snapshot_force_kernel(const int* __restrict__ rowptr, const i
 
 // Attraction of row i from its neighbours in its own or later minibatches: they
 // have not moved yet when i's minibatch runs, so this part uses the snapshot S
-// and is computed for all rows before the sweep (warp per row; rows with more
-// than kBigRow such edges get a whole block from attr_old_big_kernel).
+// and is computed for all rows before the sweep (edge_pass_kernel, warp per row;
+// rows with more than kBigRow edges get a whole block from edge_pass_big_kernel).
 constexpr int kBigRow = 8192;
 
 __device__ __forceinline__ void attr_term(float2 me, float2 p, float invK, float& ax, float& ay) {
@@ -592,11 +612,15 @@ __device__ __forceinline__ void attr_term(float2 me, float2 p, float invK, float
     ay = fmaf(dy, sc, ay);
 }
 
-// lane-strided sum over edges [e0, e1) of row `me`, 4 loads in flight per lane
-__device__ __forceinline__ void attr_sum_strided(const int* __restrict__ colids,
-                                                 const float2* __restrict__ S, float2 me, int e0,
-                                                 int e1, int start, int stride, float invK,
-                                                 float& ax, float& ay) {
+// One pass over every row's edges at the snapshot S: the attraction of the
+// neighbours in the row's own or later minibatches (edges from split[i] on; they
+// have not moved when the row's minibatch does) and, unless repulse_neighbors, the
+// repulsion the tree gave the neighbours, taken back out of rep. A warp per row;
+// rows with more than kBigRow edges are left to edge_pass_big_kernel.
+__device__ __forceinline__ void edge_terms_strided(const int* __restrict__ colids,
+                                                   const float2* __restrict__ S, float2 me, int e0,
+                                                   int e1, int es, int start, int stride, float invK,
+                                                   bool rn, float& ax, float& ay, float& qx, float& qy) {
     for (int e = e0 + start; e < e1; e += 4 * stride) {
         int j[4];
         float2 p[4];
@@ -605,61 +629,83 @@ __device__ __forceinline__ void attr_sum_strided(const int* __restrict__ colids,
 #pragma unroll
         for (int k = 0; k < 4; k++) p[k] = j[k] >= 0 ? S[j[k]] : me;
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (j[k] >= 0) attr_term(me, p[k], invK, ax, ay);
+        for (int k = 0; k < 4; k++) {
+            if (j[k] < 0) continue;
+            if (e + k * stride >= es) attr_term(me, p[k], invK, ax, ay);
+            if (!rn) rep_pair(me.x, me.y, p[k].x, p[k].y, qx, qy);
+        }
     }
 }
 
-__global__ void attr_old_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
-                                const int* __restrict__ split, const float2* __restrict__ S, int n,
-                                float invK, float2* __restrict__ old) {
+__global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
+                                 const int* __restrict__ split, const float2* __restrict__ S, int n,
+                                 float invK, int rn, float2* __restrict__ old, float2* __restrict__ rep) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
     const int i = warp;
-    const int e0 = split[i], e1 = rowptr[i + 1];
-    if (e1 - e0 > kBigRow) return;   // attr_old_big_kernel
+    const int e0 = rowptr[i], e1 = rowptr[i + 1];
+    if (e1 - e0 > kBigRow) return;   // edge_pass_big_kernel
     const float2 me = S[i];
-    float ax = 0.f, ay = 0.f;
-    attr_sum_strided(colids, S, me, e0, e1, lane, 32, invK, ax, ay);
+    float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
+    edge_terms_strided(colids, S, me, e0, e1, split[i], lane, 32, invK, rn != 0, ax, ay, qx, qy);
     ax = warp_sum(ax);
     ay = warp_sum(ay);
-    if (lane == 0) old[i] = make_float2(ax, ay);
-}
-
-__global__ void __launch_bounds__(1024) attr_old_big_kernel(
-    const int* __restrict__ rowptr, const int* __restrict__ colids, const int* __restrict__ split,
-    const float2* __restrict__ S, const int* __restrict__ big_rows, float invK,
-    float2* __restrict__ old) {
-    __shared__ float2 s_w[32];
-    const int i = big_rows[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float2 me = S[i];
-    float ax = 0.f, ay = 0.f;
-    attr_sum_strided(colids, S, me, split[i], rowptr[i + 1], threadIdx.x, blockDim.x, invK, ax, ay);
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    if (lane == 0) s_w[warp] = make_float2(ax, ay);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float sx = 0.f, sy = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-            sx += s_w[w].x;
-            sy += s_w[w].y;
+    if (!rn) {
+        qx = warp_sum(qx);
+        qy = warp_sum(qy);
+    }
+    if (lane == 0) {
+        old[i] = make_float2(ax, ay);
+        if (!rn) {
+            const float2 r = rep[i];
+            rep[i] = make_float2(r.x - qx, r.y - qy);
         }
-        old[i] = make_float2(sx, sy);
     }
 }
 
-// Level sets of the sweep. Row i reads its neighbours in earlier minibatches at
-// their new positions, so it can run once they have moved; its neighbours in its
-// own or later minibatches are read at the snapshot, whatever the order. With
+__global__ void __launch_bounds__(1024) edge_pass_big_kernel(
+    const int* __restrict__ rowptr, const int* __restrict__ colids, const int* __restrict__ split,
+    const float2* __restrict__ S, const int* __restrict__ big_rows, float invK, int rn,
+    float2* __restrict__ old, float2* __restrict__ rep) {
+    __shared__ float4 s_w[32];
+    const int i = big_rows[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float2 me = S[i];
+    float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
+    edge_terms_strided(colids, S, me, rowptr[i], rowptr[i + 1], split[i], threadIdx.x, blockDim.x, invK,
+                       rn != 0, ax, ay, qx, qy);
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    qx = warp_sum(qx);
+    qy = warp_sum(qy);
+    if (lane == 0) s_w[warp] = make_float4(ax, ay, qx, qy);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            t.x += s_w[w].x;
+            t.y += s_w[w].y;
+            t.z += s_w[w].z;
+            t.w += s_w[w].w;
+        }
+        old[i] = make_float2(t.x, t.y);
+        if (!rn) {
+            const float2 r = rep[i];
+            rep[i] = make_float2(r.x - t.z, r.y - t.w);
+        }
+    }
+}
+
+// The sweep. Row i reads its neighbours in earlier minibatches at their new
+// positions, so it can run once they have moved; its neighbours in its own or
+// later minibatches are read at the snapshot, whatever the order. With
 // level(i) = 1 + max level of i's earlier-minibatch neighbours (1 when there are
 // none), all rows of one level are independent of each other and depend only on
-// lower levels: running the levels in order, one grid barrier apart, computes
-// exactly the sequential minibatch sweep. A row with many earlier-minibatch edges
-// is cut into segments (tasks); the last segment to finish combines the segment
-// sums in order.
+// lower levels, and any order that runs a row after its earlier-minibatch
+// neighbours computes exactly the sequential minibatch sweep. Tasks are stored
+// level by level; a row with many earlier-minibatch edges is cut into segments
+// (tasks) and the last segment to finish combines the segment sums in order.
 struct SweepArgs {
     const int* rowptr;
     const int* colids;
@@ -673,7 +719,6 @@ struct SweepArgs {
     float2* seg_sum;
     int* seg_cnt;            // per row: segments finished (reset per launch)
     double* e_row;           // |ct|^2 of every row
-    unsigned* bar;
     int* status;
     int nlevels;
     int first_level;         // levels before it are done by level0_kernel
@@ -682,6 +727,26 @@ struct SweepArgs {
 };
 
 constexpr int kSegEdges = 128;   // earlier-minibatch edges per task (4 gathers per lane)
+
+// New positions are published with one 64-bit store (single-copy atomic), and
+// before the sweep every slot holds kUnset (two NaNs no position can take): a
+// row that needs a moved neighbour reads the slot until it is set. The position
+// is its own ready flag.
+constexpr unsigned long long kUnset = ~0ull;
+
+__device__ __forceinline__ void publish_pos(float2* p, float x, float y) {
+    const unsigned long long v =
+        (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long read_pos(const float2* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ float2 unpack_pos(unsigned long long v) {
+    return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
+}
 
 // The row's update: ct = attraction (this iteration's moved neighbours sx,sy +
 // the not-yet-moved ones od) + repulsion rp scaled by -RK^2; me = start position.
@@ -701,15 +766,15 @@ __device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float2 me,
         nx = fmaf(sc, gx, me.x);
         ny = fmaf(sc, gy, me.y);
     }
-    a.bnew[i] = make_float2(nx, ny);
     a.e_row[i] = (double)fmaf(fx, fx, fy * fy);
+    publish_pos(&a.bnew[i], nx, ny);
 }
 
 // Everything a task needs that the sweep does not change: the task record, the
 // row's start position, repulsion and not-yet-moved attraction, and the column
-// ids of its first 128 edges (4 per lane). Loaded for the next level before a
-// warp enters the level barrier, so that after it only the moved neighbours'
-// positions remain to be read.
+// ids of its first 128 edges (4 per lane). A warp loads its next task's while it
+// runs the current one, so that a task then waits only for the moved neighbours'
+// positions.
 struct TaskPre {
     int4 tk;
     float2 me, rp, od;
@@ -729,29 +794,74 @@ __device__ __forceinline__ void task_prefetch(const SweepArgs& a, int t, int lan
     }
 }
 
-__device__ __forceinline__ void task_run(const SweepArgs& a, const TaskPre& p, int lane) {
+// The first level: rows with no neighbour in an earlier minibatch. Nothing they
+// read moves during the sweep, so they need no waiting: one thread per row.
+__global__ void level0_kernel(SweepArgs a) {
+    const int t1 = a.lvl_ptr[1];
+    for (int t = a.lvl_ptr[0] + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
+        const int i = a.tasks[t].x;
+        finish_row(a, i, a.bold[i], a.rep[i], a.old[i], 0.f, 0.f);
+    }
+}
+
+// Dataflow sweep: no level barriers. Warps take the level-ordered tasks round
+// robin (task t goes to warp t mod warps), so every warp meets its tasks in level
+// order; a task reads each moved neighbour's slot until it is published. The
+// lowest-level unfinished task always has its inputs, because everything below
+// its level is finished or being finished by warps that are not waiting on it,
+// and all CTAs are resident (cooperative launch): the sweep cannot stall. Every
+// wait is bounded (BL_ETIMEOUT).
+struct Gather4 {
+    int j[4];
+    unsigned long long v[4];
+};
+
+// Reads the published positions of up to 4 ids per lane; false when the wait gave up.
+__device__ __forceinline__ bool gather_wait(const SweepArgs& a, Gather4& g, int lane) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) g.v[k] = g.j[k] >= 0 ? read_pos(&a.bnew[g.j[k]]) : 0ull;
+    unsigned long long t0 = 0;
+    for (unsigned spin = 0;; ++spin) {
+        bool pending = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) pending |= g.j[k] >= 0 && g.v[k] == kUnset;
+        if (!__any_sync(0xffffffffu, pending)) return true;
+        __nanosleep(64);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (g.j[k] >= 0 && g.v[k] == kUnset) g.v[k] = read_pos(&a.bnew[g.j[k]]);
+        if ((spin & 127u) == 127u) {
+            int bad = 0;
+            if (lane == 0) {
+                if (t0 == 0) t0 = global_ns();
+                if (ld_volatile_i32(a.status) != 0) bad = 1;
+                else if (global_ns() - t0 > kWaitLimitNs) {
+                    atomicCAS(a.status, 0, (int)BL_ETIMEOUT);
+                    bad = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane) {
     const int i = p.tk.x;
     const int seg = p.tk.w & 0xFFFF, nseg = p.tk.w >> 16;
     const float2 me = p.me;
     float sx = 0.f, sy = 0.f;
-    {   // first 128 edges: ids already in registers
-        float2 q[4];
+    Gather4 g;
 #pragma unroll
-        for (int k = 0; k < 4; k++) q[k] = p.j[k] >= 0 ? __ldcg(&a.bnew[p.j[k]]) : me;
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (p.j[k] >= 0) attr_term(me, q[k], a.invK, sx, sy);
-    }
-    for (int e = p.tk.y + 128 + lane; e < p.tk.z; e += 128) {   // 4 gathers in flight per lane
-        int j[4];
-        float2 q[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) j[k] = e + 32 * k < p.tk.z ? __ldg(&a.colids[e + 32 * k]) : -1;
-#pragma unroll
-        for (int k = 0; k < 4; k++) q[k] = j[k] >= 0 ? __ldcg(&a.bnew[j[k]]) : me;
+    for (int k = 0; k < 4; k++) g.j[k] = p.j[k];
+    for (int e = p.tk.y + lane;;) {
+        if (!gather_wait(a, g, lane)) return false;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (j[k] >= 0) attr_term(me, q[k], a.invK, sx, sy);
+            if (g.j[k] >= 0) attr_term(me, unpack_pos(g.v[k]), a.invK, sx, sy);
+        e += 128;
+        if (!__any_sync(0xffffffffu, e < p.tk.z)) break;
+#pragma unroll
+        for (int k = 0; k < 4; k++) g.j[k] = e + 32 * k < p.tk.z ? __ldg(&a.colids[e + 32 * k]) : -1;
     }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
@@ -774,50 +884,34 @@ __device__ __forceinline__ void task_run(const SweepArgs& a, const TaskPre& p, i
             }
         }
     }
+    return true;
 }
 
-// The first level: rows with no neighbour in an earlier minibatch. Nothing they
-// read moves during the sweep, so they need no barrier: one thread per row.
-__global__ void level0_kernel(SweepArgs a) {
-    const int t1 = a.lvl_ptr[1];
-    for (int t = a.lvl_ptr[0] + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
-        const int i = a.tasks[t].x;
-        finish_row(a, i, a.bold[i], a.rep[i], a.old[i], 0.f, 0.f);
-    }
-}
-
-__global__ void __launch_bounds__(kSweepThreads) level_sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads) dataflow_sweep_kernel(SweepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    GridBarrier bar{a.bar, a.status, gridDim.x, 0u};
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0)
-        for (int q = 0; q < a.first_level && q < a.nlevels; q++) a.trace[q] = global_ns();
-    TaskPre cur;
     const int l0 = a.first_level;
-    bool have = l0 < a.nlevels && a.lvl_ptr[l0] + gw < a.lvl_ptr[l0 + 1];
-    if (have) task_prefetch(a, a.lvl_ptr[l0] + gw, lane, cur);
-    for (int l = l0; l < a.nlevels; l++) {
-        if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[l] = global_ns();
-        const int t0 = a.lvl_ptr[l] + gw, t1 = a.lvl_ptr[l + 1];
-        if (have) task_run(a, cur, lane);
-        if (t0 + nw < t1) {   // further tasks of this level: the next one loads while one runs
-            TaskPre p;
-            task_prefetch(a, t0 + nw, lane, p);
-            for (int t = t0 + nw; t < t1; t += nw) {
-                TaskPre q;
-                const bool more = t + nw < t1;
-                if (more) task_prefetch(a, t + nw, lane, q);
-                task_run(a, p, lane);
-                if (more) p = q;
-            }
+    if (l0 >= a.nlevels) return;
+    const int t1 = a.lvl_ptr[a.nlevels];
+    int t = a.lvl_ptr[l0] + gw;
+    int lnext = l0;   // trace: next level whose first task this warp may meet
+    if (a.trace && gw == 0 && lane == 0)
+        for (int q = 0; q < l0; q++) a.trace[q] = global_ns();
+    TaskPre cur;
+    if (t < t1) task_prefetch(a, t, lane, cur);
+    for (; t < t1; t += nw) {
+        if (a.trace && lane == 0) {
+            while (lnext < a.nlevels && a.lvl_ptr[lnext] < t) lnext++;
+            if (lnext < a.nlevels && a.lvl_ptr[lnext] == t) a.trace[lnext] = global_ns();
         }
-        // the next level's first task, loaded while this warp waits at the barrier
-        have = l + 1 < a.nlevels && a.lvl_ptr[l + 1] + gw < a.lvl_ptr[l + 2];
-        if (have) task_prefetch(a, a.lvl_ptr[l + 1] + gw, lane, cur);
-        if (!bar.sync()) return;
+        TaskPre nxt;
+        const bool more = t + nw < t1;
+        if (more) task_prefetch(a, t + nw, lane, nxt);   // static data of the next task
+        if (!task_run_df(a, cur, lane)) return;
+        if (more) cur = nxt;
     }
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[a.nlevels] = global_ns();
+    if (a.trace && lane == 0) atomicMax(&a.trace[a.nlevels], (unsigned long long)global_ns());
 }
 
 // energy of the iteration: fixed-order reduction of the rows' |ct|^2
@@ -928,7 +1022,8 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st) {
 }
 
 // repulsion sums of every vertex from the tree of S, neighbours taken out
-static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaStream_t st) {
+static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaStream_t st,
+                              bool correct = true) {
     BHState* s = L->bh;
     const int n = L->g->n;
     BL_CUDA_TRY(cudaMemsetAsync(s->walkcnt.p, 0, 2 * sizeof(unsigned long long), st));
@@ -937,7 +1032,7 @@ static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaSt
     walk_kernel<<<div_up(n, 256), 256, 0, st>>>(s->vals0.as<int>(), s->spos.as<float2>(), s->cnt.as<int>(),
                                                 n, s->nd_rec.as<float4>(), s->nd_aux.as<int2>(), theta2,
                                                 s->rep.as<float2>(), s->walkcnt.as<unsigned long long>());
-    if (!L->prm.repulse_neighbors)
+    if (correct && !L->prm.repulse_neighbors)
         nbr_correct_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
             L->g->rowptr.as<int>(), L->g->colids.as<int>(), S, n, s->rep.as<float2>());
     BL_CUDA_TRY(cudaGetLastError());
@@ -969,7 +1064,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
         const int lo = (i / BS) * BS;
         const int* sp = std::lower_bound(ci + rp[i], ci + rp[i + 1], lo);
         split[i] = (int)(sp - ci);
-        if (ci + rp[i + 1] - sp > kBigRow) bigrows.push_back(i);
+        if (rp[i + 1] - rp[i] > kBigRow) bigrows.push_back(i);   // edge_pass_big_kernel
         int d = 0;
         for (const int* c = ci + rp[i]; c < sp; c++) d = std::max(d, level[*c]);
         level[i] = d + 1;
@@ -1037,9 +1132,9 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
     BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(iters, 1) * sizeof(double)));
     double step = 1.0;
     for (int64_t k = 0; k < L->t; k++) step *= 0.999;
-    int occ = 0;
-    BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_sweep_kernel, kSweepThreads, 0));
     int per_sm = 2;   // sweep CTAs per SM (measured best on R-MAT 20); BL_BH_SWEEP_CTAS overrides it
+    int occ = 0;
+    BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dataflow_sweep_kernel, kSweepThreads, 0));
     if (const char* e = std::getenv("BL_BH_SWEEP_CTAS")) per_sm = std::max(1, std::atoi(e));
     const int G = std::max(1, std::min(occ, per_sm)) * device_sm_count();
     const int nep = std::min(1024, div_up(n, 1024));
@@ -1047,15 +1142,18 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         const float2* S = L->pos.as<float2>();
         float2* bnew = L->pos2.as<float2>();
         BL_TRY(bh_build(L, S, st));
-        BL_TRY(bh_repulsion(L, S, theta, st));
-        // attraction from neighbours that have not moved yet, all rows at once
-        attr_old_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
-            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K,
-            s->old.as<float2>());
+        BL_TRY(bh_repulsion(L, S, theta, st, false));
+        // one pass over the edges: attraction from neighbours that have not moved
+        // yet, all rows at once, and the neighbour correction of the tree repulsion
+        const int rn = L->prm.repulse_neighbors;
+        edge_pass_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, rn,
+            s->old.as<float2>(), s->rep.as<float2>());
         if (s->nbig > 0)
-            attr_old_big_kernel<<<s->nbig, 1024, 0, st>>>(L->g->rowptr.as<int>(), L->g->colids.as<int>(),
-                                                          s->split.as<int>(), S, s->bigrows.as<int>(),
-                                                          1.0f / L->prm.K, s->old.as<float2>());
+            edge_pass_big_kernel<<<s->nbig, 1024, 0, st>>>(L->g->rowptr.as<int>(), L->g->colids.as<int>(),
+                                                           s->split.as<int>(), S, s->bigrows.as<int>(),
+                                                           1.0f / L->prm.K, rn, s->old.as<float2>(),
+                                                           s->rep.as<float2>());
         BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, st));
         BL_TRY(layout_reset_sync_words(L, st));
         SweepArgs a{};
@@ -1071,7 +1169,6 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         a.seg_sum = s->seg_sum.as<float2>();
         a.seg_cnt = s->seg_cnt.as<int>();
         a.e_row = s->e_row.as<double>();
-        a.bar = layout_barrier_word(L);
         a.status = static_cast<int*>(L->status.p);
         a.nlevels = s->nlevels;
         a.invK = 1.0f / L->prm.K;
@@ -1086,12 +1183,13 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
             L->trace_count = s->nlevels + 1;
         }
         a.first_level = s->nlevels > 0 ? 1 : 0;
+        BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), st));   // every slot kUnset
         if (a.first_level == 1) {
             const int n0 = s->lvl0_rows;
             level0_kernel<<<std::max(1, std::min(div_up(n0, 256), 8 * device_sm_count())), 256, 0, st>>>(a);
         }
         void* args[] = {&a};
-        BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)level_sweep_kernel, dim3(G),
+        BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dataflow_sweep_kernel, dim3(G),
                                                 dim3(kSweepThreads), args, 0, st));
         row_energy_kernel<<<nep, 256, 0, st>>>(s->e_row.as<double>(), n, s->epart.as<double>());
         energy_parts_kernel<<<1, 32, 0, st>>>(s->epart.as<double>(), nep, L->energy.as<double>() + t);
