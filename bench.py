@@ -258,7 +258,10 @@ def run_exact(args, rank, world, local):
                 "steps": e2e_steps},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9,
                      "unit": "G pair-interactions/s (1 SFU reciprocal per pair)",
-                     "frac": achieved / peak_pairs, "traffic": None,
+                     "frac": achieved / peak_pairs,
+                     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch
+                     # (10 iterations), profiles/exact_grid_kernel_ba65536.md
+                     "traffic": 2962176, "traffic_unit": "bytes per launch",
                      "kernel": "exact_grid_kernel",
                      "peak_source": f"{SMS} SMs x {MUFU_PER_CLK_PER_SM} SFU lanes/clk x "
                                     f"{sm_max:.0f} MHz ({src} sm_max_mhz)"},
