@@ -260,7 +260,7 @@ def run_exact(args, rank, world, local):
                      "unit": "G pair-interactions/s (1 SFU reciprocal per pair)",
                      "frac": achieved / peak_pairs,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch
-                     # (10 iterations), profiles/exact_grid_kernel_ba65536.md
+                     # (10 iterations) of this kernel on this workload
                      "traffic": 2962176, "traffic_unit": "bytes per launch",
                      "kernel": "exact_grid_kernel",
                      "peak_source": f"{SMS} SMs x {MUFU_PER_CLK_PER_SM} SFU lanes/clk x "
