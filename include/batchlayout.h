@@ -129,14 +129,37 @@ bl_status bl_layout_init(const bl_graph *g, const float *xy, uint64_t seed, int6
                          const bl_force_params *params, bl_layout **out);
 
 /* Replaces the positions (host, 2n floats) and the iteration counter. */
+/* Greedy initialisation (Section 3.6, Algorithm 3): a layout whose positions
+ * come from a depth-first placement starting at v0 = (0, 0): each vertex U taken
+ * from the stack puts its not yet placed neighbours, in CSR order, on the unit
+ * circle around U at angles 0, d, 2d, ... degrees, d = 360/deg(U) (PI = 3.1416
+ * as the paper prints it), formed in double and stored as FP32. v0 < 0 draws the
+ * start vertex as SplitMix64(seed) output 0 mod n. Vertices outside v0's
+ * component keep the seeded random positions of bl_layout_init(seed). Host-side
+ * (the walk's order defines the layout); synchronises. */
+bl_status bl_layout_init_greedy(const bl_graph *g, int64_t v0, uint64_t seed,
+                                const bl_force_params *params, bl_layout **out);
+
 bl_status bl_layout_set_positions(bl_layout *L, const float *xy, int64_t start_iter);
 
 /* Runs `iters` iterations with minibatch size `batch` (1 <= batch <= 8192)
- * in mode BL_EXACT or BL_BH (theta: MAC threshold, the paper uses 1.2).
- * Continues the step schedule from the layout's iteration counter. Queued on
- * the stream; returns after the launch (errors of the device-side waits are
- * reported by the next synchronising call). */
+ * in mode BL_EXACT or BL_BH (theta: MAC threshold, the paper uses 1.2) —
+ * Algorithm 2 with Section 2.2's forces, Algorithm S5 for BL_BH. Continues the
+ * step schedule from the layout's iteration counter; runs of k and m
+ * iterations give the same positions and energies, bit for bit, as one run of
+ * k + m. Synchronises; BL_ETIMEOUT if a bounded device-side wait gave up. */
 bl_status bl_layout_run(bl_layout *L, int32_t iters, int32_t batch, bl_mode mode, float theta);
+
+/* Runs at most max_iters iterations and stops after the first iteration whose
+ * energy differs from the previous one by at most tol * max(E_prev, 1) (Section
+ * 4.5 runs until the difference is below 1e-6; read relatively). The previous
+ * one may come from the layout's last run. The result equals stopping there
+ * exactly: iterations run in chunks, and a chunk in which the rule holds is
+ * rolled back and re-run to that iteration. *iters_done receives the iterations
+ * run, *converged 1 if the rule held (both may be NULL); bl_energy_history then
+ * returns the call's whole history. Synchronises. */
+bl_status bl_layout_run_until(bl_layout *L, int32_t max_iters, int32_t batch, bl_mode mode,
+                              float theta, double tol, int32_t *iters_done, int32_t *converged);
 
 /* Copies positions to host (2n floats; cap_floats >= 2n). Synchronises. */
 bl_status bl_positions(const bl_layout *L, float *xy, int64_t cap_floats);

@@ -86,6 +86,8 @@ def _declare(lib):
         "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
         "bl_layout_run_batch": [P, i32, i32, i32],
         "bl_debug_barrier_timeout": [i32],
+        "bl_layout_init_greedy": [P, i64, u64, P, PP],
+        "bl_layout_run_until": [P, i32, i32, ctypes.c_int, f32, f64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name, None)
@@ -228,6 +230,16 @@ class Layout:
         _check(_lib.bl_layout_run(self._h, int(iters), int(batch), MODES[mode], float(theta)))
         return self
 
+    def run_until(self, max_iters: int, batch: int = 256, mode: str = "exact",
+                  theta: float = THETA_DEFAULT, tol: float = 1e-6):
+        """Runs until the relative energy change falls to tol (bl_layout_run_until).
+        Returns (iterations run, converged)."""
+        it = ctypes.c_int32(0)
+        cv = ctypes.c_int32(0)
+        _check(_lib.bl_layout_run_until(self._h, int(max_iters), int(batch), MODES[mode], float(theta),
+                                        float(tol), ctypes.byref(it), ctypes.byref(cv)))
+        return it.value, bool(cv.value)
+
     def set_positions(self, xy, start_iter: int = 0):
         arr = np.ascontiguousarray(np.asarray(xy, dtype=np.float32).reshape(self.graph.n, 2))
         _check(_lib.bl_layout_set_positions(self._h, _ptr(arr), int(start_iter)))
@@ -312,6 +324,16 @@ class Layout:
             self.close()
         except Exception:
             pass
+
+
+def greedy_layout(graph: Graph, v0: int = -1, seed: int = 0, K: float = 1.0, R: float = 1.0,
+                  repulse_neighbors: bool = False) -> Layout:
+    """A layout initialised by the greedy placement (bl_layout_init_greedy)."""
+    prm = ForceParams(K, R, int(repulse_neighbors), -1)
+    h = ctypes.c_void_p()
+    _check(load().bl_layout_init_greedy(graph.handle, int(v0), ctypes.c_uint64(seed), ctypes.byref(prm),
+                                        ctypes.byref(h)))
+    return Layout(graph, _handle=h)
 
 
 def layout_run_noalloc(n: int, d_rowptr: int, d_colids: int, d_xy: int, iters: int, batch: int = 256,

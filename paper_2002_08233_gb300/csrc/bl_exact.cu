@@ -258,9 +258,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         }
     };
 
-    // ---- prologue: columns c >= batch(row) at the starting positions (every
-    //      column in snapshot mode); the next tile is fetched into registers while
-    //      the bulk warps add the current one -----------------------------------------
+    // ---- prologue: columns c >= batch(row), c < B-1, at the starting positions
+    //      (every column in snapshot mode); the next tile is fetched into registers
+    //      while the bulk warps add the current one -------------------------------------
     {
         const bool one_each = TQ <= T;
         float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -288,7 +288,11 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (!is_ctl) {
                 bool need[RPT];
 #pragma unroll
-                for (int m = 0; m < RPT; m++) need[m] = bi[m] >= 0 && (snapshot || bi[m] <= c);
+                // the last batch's tile is added at step 0 instead, as it is when a
+                // launch continues across an iteration boundary, so that results do
+                // not depend on how the iterations are split into launches
+                for (int m = 0; m < RPT; m++)
+                    need[m] = bi[m] >= 0 && (snapshot || (bi[m] <= c && c < B - 1));
                 add_tile(tile, nc, need);
             }
             if (!one_each) __syncthreads();
@@ -524,7 +528,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (k == 0 && s > 0) step *= 0.999;   // Algorithm 2: Step = Step * 0.999
             const float2* bold = (it & 1) ? buf1 : buf0;
             float2* bnew = (it & 1) ? buf0 : buf1;
-            const int kprev = s > 0 ? (k + B - 1) % B : -1;
+            const int kprev = (k + B - 1) % B;   // step 0: the last batch at the start positions
             float4* tile = s_tile + (size_t)(s & 1) * TQ;
             if (lane == 0) trace_mark(tk, rank, s, 0);
             if (s > 0) {
@@ -555,8 +559,11 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     bar_arrive_n(kBarTile, T);
                     return;
                 }
-                // the buffer batch kprev was written to at step s-1
-                const float2* bprev = (k == 0) ? bold : bnew;
+            }
+            {
+                // the buffer batch kprev was written to at step s-1 (step 0: the
+                // launch's start positions)
+                const float2* bprev = s == 0 ? buf0 : ((k == 0) ? bold : bnew);
                 {   // the control warp copies the tile; each lane issues 4 column pairs'
                     // loads before storing any, so the copy costs about one round trip
                     const float2* src = bprev + (size_t)kprev * BS;
@@ -603,8 +610,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         for (int s = 0; s < S; s++) {
             const int it = s / B;
             const int k = s - it * B;
-            const int kprev = s > 0 ? (k + B - 1) % B : -1;
-            const int kpn = kprev >= 0 ? min(BS, n - kprev * BS) : 0;
+            const int kprev = (k + B - 1) % B;   // step 0: the last batch at the start positions
+            const int kpn = min(BS, n - kprev * BS);
             bar_sync_n(kBarTile, T);
             if (s_ctl[0]) return;
             if (tb == 0) trace_mark(tk, rank, s, 7);
@@ -629,7 +636,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             bool need[RPT];
 #pragma unroll
             for (int m = 0; m < RPT; m++)
-                need[m] = s > 0 && bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
+                need[m] = bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
             if (tb == 0) trace_mark(tk, rank, s, 10);
             add_tile(tile, kpn, need);
             post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * CR);

@@ -359,6 +359,62 @@ bl_status bl_layout_init(const bl_graph* g, const float* xy, uint64_t seed, int6
 }
 
 
+// Greedy initialisation (Algorithm 3): a depth-first placement from v0 at (0, 0);
+// a vertex U taken from the stack puts each of its not yet placed neighbours on
+// the unit circle around U, the angle advancing by 360/deg(U) degrees after each,
+// with the paper's PI = 3.1416. Positions are formed in double and stored as FP32.
+// Vertices that v0 does not reach keep the seeded random positions. The walk is
+// inherently sequential (its order defines the layout), O(n + m) on the host.
+static void greedy_positions(const bl_graph* g, int v0, float* xy) {
+    const int n = g->n;
+    const int* rp = g->h_rowptr.data();
+    const int* ci = g->h_colids.data();
+    const double kPi = 3.1416;
+    std::vector<double> px(n), py(n);
+    std::vector<char> placed(n, 0);
+    std::vector<int> stack;
+    stack.reserve(n);
+    px[v0] = 0.0;
+    py[v0] = 0.0;
+    placed[v0] = 1;
+    stack.push_back(v0);
+    while (!stack.empty()) {
+        const int u = stack.back();
+        stack.pop_back();
+        const int deg = rp[u + 1] - rp[u];
+        const double step = deg > 0 ? 360.0 / (double)deg : 0.0;
+        double angle = 0.0;
+        for (int e = rp[u]; e < rp[u + 1]; e++) {
+            const int w = ci[e];
+            if (placed[w]) continue;
+            px[w] = px[u] + std::cos(kPi * angle / 180.0);
+            py[w] = py[u] + std::sin(kPi * angle / 180.0);
+            placed[w] = 1;
+            stack.push_back(w);
+            angle += step;
+        }
+    }
+    for (int i = 0; i < n; i++)
+        if (placed[i]) {
+            xy[2 * i] = (float)px[i];
+            xy[2 * i + 1] = (float)py[i];
+        }
+}
+
+bl_status bl_layout_init_greedy(const bl_graph* g, int64_t v0, uint64_t seed, const bl_force_params* params,
+                                bl_layout** out) {
+    if (!out) return set_error(BL_EINVAL, "bl_layout_init_greedy: out is NULL");
+    *out = nullptr;
+    if (!g) return set_error(BL_EINVAL, "bl_layout_init_greedy: NULL graph");
+    if (g->n == 0) return layout_create(g, nullptr, seed, 0, params, true, current_stream(), out);
+    if (v0 >= g->n) return set_error(BL_EINVAL, "bl_layout_init_greedy: v0 out of range");
+    if (v0 < 0) v0 = (int64_t)(splitmix64_at(seed, 0) % (uint64_t)g->n);
+    std::vector<float> xy((size_t)2 * g->n);
+    seeded_positions(g->n, seed, xy.data());
+    greedy_positions(g, (int)v0, xy.data());
+    return layout_create(g, xy.data(), seed, 0, params, true, current_stream(), out);
+}
+
 bl_status bl_layout_set_positions(bl_layout* L, const float* xy, int64_t start_iter) {
     if (!L || !xy) return set_error(BL_EINVAL, "bl_layout_set_positions: NULL argument");
     if (start_iter < 0) return set_error(BL_EINVAL, "bl_layout_set_positions: start_iter < 0");
@@ -398,6 +454,77 @@ bl_status bl_layout_run(bl_layout* L, int32_t iters, int32_t batch, bl_mode mode
     L->t += iters;
     L->vupd += n * iters;
     if (mode == BL_EXACT) L->pairs += n * (n - 1.0) * iters;
+    return BL_OK;
+}
+
+// Runs until the energy settles (Section 4.5 runs "until convergence": the
+// energy difference between successive iterations below 1e-6; read relatively,
+// |E_t - E_{t-1}| <= tol * max(E_{t-1}, 1), as energies are sums over all
+// vertices). Iterations run in chunks; when the rule holds inside a chunk, the
+// chunk's start positions are restored and only the iterations up to that point
+// are run again, so the result is exactly that of stopping there (both engines
+// give the same positions however iterations are split across launches).
+bl_status bl_layout_run_until(bl_layout* L, int32_t max_iters, int32_t batch, bl_mode mode, float theta,
+                              double tol, int32_t* iters_done, int32_t* converged) {
+    if (!L) return set_error(BL_EINVAL, "bl_layout_run_until: NULL layout");
+    if (max_iters < 0 || !(tol >= 0.0)) return set_error(BL_EINVAL, "bl_layout_run_until: bad max_iters or tol");
+    if (iters_done) *iters_done = 0;
+    if (converged) *converged = 0;
+    const int n = L->g->n;
+    cudaStream_t st = current_stream();
+    BL_TRY(L->scratch.ensure(L->alloc, (size_t)std::max(n, 1) * sizeof(float2)));
+    // the energy of the iteration before this call, when there is one
+    double prev = 0.0;
+    bool have_prev = false;
+    if (L->last_iters > 0 && L->energy.p) {
+        BL_CUDA_TRY(cudaMemcpyAsync(&prev, L->energy.as<double>() + (L->last_iters - 1), sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        BL_CUDA_TRY(cudaStreamSynchronize(st));
+        have_prev = true;
+    }
+    const int chunk = mode == BL_EXACT ? 32 : 8;
+    std::vector<double> hist;
+    int done = 0;
+    bool conv = false;
+    while (done < max_iters && !conv) {
+        const int c = std::min(chunk, max_iters - done);
+        BL_CUDA_TRY(cudaMemcpyAsync(L->scratch.p, L->pos.p, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        const int64_t t0 = L->t;
+        const double vupd0 = L->vupd, pairs0 = L->pairs;
+        BL_TRY(bl_layout_run(L, c, batch, mode, theta));
+        std::vector<double> e(c);
+        int64_t cnt = 0;
+        BL_TRY(bl_energy_history(L, e.data(), c, &cnt));
+        int stop = c;
+        for (int k = 0; k < c; k++) {
+            if (have_prev && std::fabs(e[k] - prev) <= tol * std::max(prev, 1.0)) {
+                stop = k + 1;
+                conv = true;
+                break;
+            }
+            prev = e[k];
+            have_prev = true;
+        }
+        if (conv && stop < c) {   // back to the chunk's start, then exactly `stop` iterations
+            BL_CUDA_TRY(cudaMemcpyAsync(L->pos.p, L->scratch.p, (size_t)n * sizeof(float2),
+                                        cudaMemcpyDeviceToDevice, st));
+            L->t = t0;
+            L->vupd = vupd0;
+            L->pairs = pairs0;
+            BL_TRY(bl_layout_run(L, stop, batch, mode, theta));
+        }
+        hist.insert(hist.end(), e.begin(), e.begin() + stop);
+        done += stop;
+    }
+    if (done > 0) {   // the call's whole energy history
+        BL_TRY(L->energy.ensure(L->alloc, (size_t)done * sizeof(double)));
+        BL_CUDA_TRY(cudaMemcpyAsync(L->energy.p, hist.data(), (size_t)done * sizeof(double),
+                                    cudaMemcpyHostToDevice, st));
+        BL_CUDA_TRY(cudaStreamSynchronize(st));
+        L->last_iters = done;
+    }
+    if (iters_done) *iters_done = done;
+    if (converged) *converged = conv ? 1 : 0;
     return BL_OK;
 }
 

@@ -101,18 +101,27 @@ def test_one_iteration_positions_match_oracle(core, name, maker, bs, seed):
 @pytest.mark.parametrize("n,bs", [(300, 4096), (1000, 1000), (1024, 2048)])
 def test_single_batch_update_is_normalised_step(core, n, bs):
     """With one minibatch (Jacobi), each position moves to c + Step*f/|f| with the
-    engine's own snapshot force f: checks the update arithmetic apart from the
-    force sums (FP32 rounding of c + Step*u only). For n <= 1024 the snapshot
-    hook and the run sum the same single column tile in the same order, so the
-    two forces are the same FP32 values."""
+    engine's own snapshot force f: checks the update arithmetic. The run adds the
+    single column tile in its critical pass and the snapshot hook in its bulk
+    pass, so the two FP32 forces differ by rounding, at most eps = 1e-5 of the
+    sum of the term magnitudes m_i (the force bound); that turns the unit vector
+    by at most ~eps*m_i/|f_i|. Each vertex is held to
+    Step * 2 * eps * m_i / |f_i| plus the FP32 rounding of c + Step*u."""
     g = synth.erdos_renyi(n, 5.0, n)
     xy = synth.uniform_positions(n, n)
     _, L = _layout(core, g, xy, start_iter=40)
     f = L.debug_forces("exact").astype(np.float64)
+    _, mag = oracle.forces(g, xy, nthreads=NCPU)
     L.run(1, bs, "exact")
     step = 0.999 ** 40
-    expect = xy + step * f / np.linalg.norm(f, axis=1)[:, None]
-    assert np.max(np.abs(L.positions() - expect)) <= 4e-7 * (1.0 + np.abs(expect).max())
+    nf = np.linalg.norm(f, axis=1)
+    expect = xy + step * f / nf[:, None]
+    err = np.linalg.norm(L.positions() - expect, axis=1)
+    tol = step * 2 * TOL_FORCE_EXACT * mag / nf + 4e-7 * (1.0 + np.abs(expect).max())
+    assert np.all(err <= tol), (err / tol).max()
+    # and the update arithmetic itself, where the direction is well conditioned
+    well = TOL_FORCE_EXACT * mag / nf < 1e-3
+    assert well.mean() > 0.5
 
 
 def test_step_schedule_continues_across_runs(core):
@@ -224,3 +233,21 @@ def test_bulk_shape_does_not_change_results(core, threads):
             os.environ.pop("BL_EXACT_THREADS", None)
     assert np.array_equal(out["512"][0], out[threads][0])
     assert np.array_equal(out["512"][1], out[threads][1])
+
+
+@pytest.mark.parametrize("n,bs", [(300, 64), (1024, 128), (3000, 256), (200, 512)])
+def test_split_runs_equal_one_run(core, n, bs):
+    """A run of 6 iterations gives the same positions and energies, bit for bit,
+    as runs of 1 + 2 + 3 iterations: the engine's sums do not depend on where the
+    launches start (B = 1 included: n = 200 in one minibatch of 512)."""
+    g = synth.erdos_renyi(n, 5.0, n)
+    xy = synth.uniform_positions(n, n)
+    _, A = _layout(core, g, xy)
+    A.run(6, bs, "exact")
+    _, P = _layout(core, g, xy)
+    e = []
+    for k in (1, 2, 3):
+        P.run(k, bs, "exact")
+        e.extend(P.energy_history().tolist())
+    assert np.array_equal(A.positions(), P.positions())
+    assert np.array_equal(A.energy_history(), np.array(e))
