@@ -51,8 +51,8 @@ def _load():
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i32, f64, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
-            lib.orc_forces.argtypes = [i32, P, P, P, f64, f64, i32, i32, f64, i32, i32, i32, P, P]
-            lib.orc_run.argtypes = [i32, P, P, P, i32, i32, i32, f64, f64, f64, i32, i64, i32, P]
+            lib.orc_forces.argtypes = [i32, P, P, P, f64, f64, i32, i32, i32, f64, i32, i32, i32, P, P]
+            lib.orc_run.argtypes = [i32, P, P, P, i32, i32, i32, f64, f64, f64, i32, i32, i64, i32, P]
             lib.orc_morton.argtypes = [i32, P, P, P, P]
             lib.orc_bh_tree.argtypes = [i32, P, P, P, P, i32, P, P, P, P, P, P, P]
             lib.orc_bh_interactions.argtypes = [i32, P, P, f64, P, P]
@@ -82,10 +82,11 @@ def _check(rc: int, what: str):
 
 
 def forces(g, xy, K=1.0, R=1.0, repulse_neighbors=False, mode=EXACT, theta=THETA_DEFAULT,
-           lo=0, hi=None, nthreads=1):
+           lo=0, hi=None, nthreads=1, a=2):
     """One-snapshot combined forces f(i, c) for i in [lo, hi) (Section 2.2;
-    BH repulsion per Algorithms S3/S4). Returns (f[hi-lo, 2], mag[hi-lo]) where
-    mag_i is the sum of the magnitudes of the terms that make up f(i, c)."""
+    BH repulsion per Algorithms S3/S4; attraction d^a/K, a = 2 by default).
+    Returns (f[hi-lo, 2], mag[hi-lo]) where mag_i is the sum of the magnitudes
+    of the terms that make up f(i, c)."""
     lib = _load()
     n = g.n
     hi = n if hi is None else hi
@@ -93,22 +94,22 @@ def forces(g, xy, K=1.0, R=1.0, repulse_neighbors=False, mode=EXACT, theta=THETA
     x = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(n, 2))
     f = np.zeros((max(hi - lo, 0), 2), dtype=np.float64)
     mag = np.zeros(max(hi - lo, 0), dtype=np.float64)
-    rc = lib.orc_forces(n, _ptr(rp), _ptr(ci), _ptr(x), K, R, int(repulse_neighbors), mode,
+    rc = lib.orc_forces(n, _ptr(rp), _ptr(ci), _ptr(x), K, R, int(a), int(repulse_neighbors), mode,
                         theta, lo, hi, nthreads, _ptr(f) if f.size else None, _ptr(mag) if mag.size else None)
     _check(rc, "forces")
     return f, mag
 
 
 def run(g, xy, iters, batch, mode=EXACT, theta=THETA_DEFAULT, K=1.0, R=1.0,
-        repulse_neighbors=False, start_iter=0, nthreads=1):
-    """Algorithm 2 (exact) or Algorithm S5 (BH): returns (positions float64[n,2],
-    energy per iteration float64[iters])."""
+        repulse_neighbors=False, start_iter=0, nthreads=1, a=2):
+    """Algorithm 2 (exact) or Algorithm S5 (BH) with attraction d^a/K: returns
+    (positions float64[n,2], energy per iteration float64[iters])."""
     lib = _load()
     n = g.n
     rp, ci = _csr(g)
     x = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(n, 2)).copy()
     e = np.zeros(max(iters, 1), dtype=np.float64)
-    rc = lib.orc_run(n, _ptr(rp), _ptr(ci), _ptr(x), iters, batch, mode, theta, K, R,
+    rc = lib.orc_run(n, _ptr(rp), _ptr(ci), _ptr(x), iters, batch, mode, theta, K, R, int(a),
                      int(repulse_neighbors), start_iter, nthreads, _ptr(e))
     _check(rc, "run")
     return x, e[:iters]

@@ -55,6 +55,11 @@
  *       Leaves always sum their vertices directly (each with its own
  *       distance); vertex i itself is skipped by index. There is no
  *       containment test.
+ *   R19 (a,r)-energy models (Section 2.2; Section 4.1 says the software has
+ *       four variants from the ForceAtlas2 paper): attraction magnitude
+ *       d^a / K for a in {0, 1, 2, 3}, repulsion as R1 (r = -1), i.e. LinLog
+ *       (0,-1), ForceAtlas (1,-1), Fruchterman-Reingold (2,-1) and (3,-1).
+ *       d^a is formed by repeated multiplication.
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,14 +81,17 @@
 /* Force law, Section 2.2 (reading R1)                                         */
 /* -------------------------------------------------------------------------- */
 
-/* f_a(i,j) * (c_j - c_i)/|c_i - c_j| with f_a = |c_i - c_j|^2 / K */
-static void attractive_term(double xi, double yi, double xj, double yj, double K,
+/* f_a(i,j) * (c_j - c_i)/|c_i - c_j| with f_a = |c_i - c_j|^a / K (the
+ * (a,r)-energy model of Section 2.2; a = 2 is Fruchterman-Reingold, R1/R19) */
+static void attractive_term(double xi, double yi, double xj, double yj, double K, int a,
                             double *tx, double *ty)
 {
     double dx = xj - xi, dy = yj - yi;
     double d = sqrt(dx * dx + dy * dy);
     if (d == 0.0) { *tx = 0.0; *ty = 0.0; return; }
-    double fa = d * d / K;
+    double fa = 1.0;
+    for (int k = 0; k < a; k++) fa *= d;
+    fa /= K;
     *tx = fa * dx / d;
     *ty = fa * dy / d;
 }
@@ -105,7 +113,7 @@ static void repulsive_term(double xi, double yi, double xj, double yj, double K,
 /* -------------------------------------------------------------------------- */
 
 static void exact_force(int i, int n, const int *rowptr, const int *colids, const double *xy,
-                        double K, double R, int repulse_neighbors,
+                        double K, double R, int a, int repulse_neighbors,
                         double *fx, double *fy, double *mag)
 {
     double sx = 0.0, sy = 0.0, m = 0.0, tx, ty;
@@ -115,7 +123,7 @@ static void exact_force(int i, int n, const int *rowptr, const int *colids, cons
         int is_edge = 0;
         if (k < kend && colids[k] == j) { is_edge = 1; k++; }   /* merge of sorted colids */
         if (is_edge) {
-            attractive_term(xi, yi, xy[2 * j], xy[2 * j + 1], K, &tx, &ty);
+            attractive_term(xi, yi, xy[2 * j], xy[2 * j + 1], K, a, &tx, &ty);
             sx += tx; sy += ty; m += sqrt(tx * tx + ty * ty);
         }
         if (j != i && (!is_edge || repulse_neighbors)) {
@@ -328,14 +336,14 @@ static void tree_repulsion(const otree *t, int v, int i, double xi, double yi, f
  * on the snapshot, minus exact neighbour terms at the snapshot unless
  * repulse_neighbors (R2, R7). */
 static void bh_force(int i, const int *rowptr, const int *colids, const double *live,
-                     const otree *t, float theta, double K, double R, int repulse_neighbors,
+                     const otree *t, float theta, double K, double R, int a, int repulse_neighbors,
                      double *fx, double *fy, double *mag)
 {
     double sx = 0.0, sy = 0.0, m = 0.0, tx, ty;
     double xi = live[2 * i], yi = live[2 * i + 1];
     for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
         int j = colids[k];
-        attractive_term(xi, yi, live[2 * j], live[2 * j + 1], K, &tx, &ty);
+        attractive_term(xi, yi, live[2 * j], live[2 * j + 1], K, a, &tx, &ty);
         sx += tx; sy += ty; m += sqrt(tx * tx + ty * ty);
     }
     double rx = 0.0, ry = 0.0, rm = 0.0;
@@ -377,9 +385,10 @@ static int check_csr(int n, const int *rowptr, const int *colids)
  * the FP32-rounded positions). nthreads > 1 spreads the vertices over OpenMP
  * threads; results do not depend on it. */
 int orc_forces(int n, const int *rowptr, const int *colids, const double *xy,
-               double K, double R, int repulse_neighbors, int mode, double theta,
+               double K, double R, int a, int repulse_neighbors, int mode, double theta,
                int lo, int hi, int nthreads, double *f_out, double *mag_out)
 {
+    if (a < 0 || a > 3) return ORC_EINVAL;
     if (check_csr(n, rowptr, colids) != ORC_OK) return ORC_EINVAL;
     if (lo < 0 || hi > n || lo > hi) return ORC_EINVAL;
 #ifdef _OPENMP
@@ -392,7 +401,7 @@ int orc_forces(int n, const int *rowptr, const int *colids, const double *xy,
 #pragma omp parallel for schedule(dynamic, 16) if (nthreads > 1)
 #endif
         for (int i = lo; i < hi; i++)
-            exact_force(i, n, rowptr, colids, xy, K, R, repulse_neighbors,
+            exact_force(i, n, rowptr, colids, xy, K, R, a, repulse_neighbors,
                         &f_out[2 * (i - lo)], &f_out[2 * (i - lo) + 1], mag_out ? &mag_out[i - lo] : NULL);
         return ORC_OK;
     }
@@ -407,7 +416,7 @@ int orc_forces(int n, const int *rowptr, const int *colids, const double *xy,
 #pragma omp parallel for schedule(dynamic, 16) if (nthreads > 1)
 #endif
         for (int i = lo; i < hi; i++)
-            bh_force(i, rowptr, colids, xy, &t, (float)theta, K, R, repulse_neighbors,
+            bh_force(i, rowptr, colids, xy, &t, (float)theta, K, R, a, repulse_neighbors,
                      &f_out[2 * (i - lo)], &f_out[2 * (i - lo) + 1], mag_out ? &mag_out[i - lo] : NULL);
     }
     tree_free(&t);
@@ -422,9 +431,10 @@ int orc_forces(int n, const int *rowptr, const int *colids, const double *xy,
  * nthreads > 1 parallelises the force loop of each minibatch (Algorithm 2's
  * ParFor); results do not depend on it. */
 int orc_run(int n, const int *rowptr, const int *colids, double *xy,
-            int iters, int BS, int mode, double theta, double K, double R,
+            int iters, int BS, int mode, double theta, double K, double R, int a,
             int repulse_neighbors, long long start_iter, int nthreads, double *energy_out)
 {
+    if (a < 0 || a > 3) return ORC_EINVAL;
     if (check_csr(n, rowptr, colids) != ORC_OK) return ORC_EINVAL;
     if (iters < 0 || BS <= 0 || start_iter < 0) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
@@ -459,10 +469,10 @@ int orc_run(int n, const int *rowptr, const int *colids, double *xy,
 #endif
             for (int i = lo; i < hi; i++) {
                 if (mode == ORC_EXACT)
-                    exact_force(i, n, rowptr, colids, xy, K, R, repulse_neighbors,
+                    exact_force(i, n, rowptr, colids, xy, K, R, a, repulse_neighbors,
                                 &ct[2 * (i - lo)], &ct[2 * (i - lo) + 1], NULL);
                 else
-                    bh_force(i, rowptr, colids, xy, &tree, (float)theta, K, R, repulse_neighbors,
+                    bh_force(i, rowptr, colids, xy, &tree, (float)theta, K, R, a, repulse_neighbors,
                              &ct[2 * (i - lo)], &ct[2 * (i - lo) + 1], NULL);
             }
             /* then the update of the minibatch */

@@ -467,3 +467,46 @@ def test_greedy_init_tree_edges_have_unit_length():
         for k in range(g.rowptr[i], g.rowptr[i + 1]):
             lens.append(np.linalg.norm(x[g.colids[k]] - x[i]))
     assert np.allclose(lens, 1.0, atol=1e-12)
+
+
+# ---- (a,r)-energy models (Section 2.2): attraction d^a / K, repulsion R K^2 / d ----
+
+@pytest.mark.parametrize("a", [0, 1, 2, 3])
+@pytest.mark.parametrize("K,R", [(1.0, 1.0), (0.5, 2.0), (2.0, 0.5)])
+def test_model_two_vertex_equilibrium(a, K, R):
+    """d^a / K = R K^2 / d at d* = (R K^3)^(1/(a+1)): zero net force there,
+    repulsion inside, attraction outside."""
+    dstar = (R * K ** 3) ** (1.0 / (a + 1))
+    g, xy = two_vertex(dstar)
+    f, mag = oracle.forces(g, xy, K=K, R=R, a=a, repulse_neighbors=True)
+    assert np.max(np.abs(f)) <= 1e-12 * mag.max()
+    g, xy = two_vertex(0.5 * dstar)
+    f, _ = oracle.forces(g, xy, K=K, R=R, a=a, repulse_neighbors=True)
+    assert f[0, 0] < 0 and f[1, 0] > 0
+    g, xy = two_vertex(2.0 * dstar)
+    f, _ = oracle.forces(g, xy, K=K, R=R, a=a, repulse_neighbors=True)
+    assert f[0, 0] > 0 and f[1, 0] < 0
+
+
+@pytest.mark.parametrize("a,expect", [(0, 0.5), (1, 1.5), (2, 4.5), (3, 13.5)])
+def test_model_attraction_closed_form(a, expect):
+    """One edge of length d = 3, K = 2: |f| = 3^a / 2 towards the other end
+    (neighbours do not repel by default)."""
+    g, xy = two_vertex(3.0)
+    f, _ = oracle.forces(g, xy, K=2.0, a=a)
+    assert f[0] == pytest.approx([expect, 0.0], abs=1e-13)
+    assert f[1] == pytest.approx([-expect, 0.0], abs=1e-13)
+
+
+def test_model_default_is_fruchterman_reingold():
+    g = synth.erdos_renyi(60, 5.0, 1)
+    xy = synth.uniform_positions(60, 1)
+    f2, m2 = oracle.forces(g, xy, a=2)
+    fd, md = oracle.forces(g, xy)
+    assert np.array_equal(f2, fd) and np.array_equal(m2, md)
+
+
+def test_model_out_of_range_is_rejected():
+    g, xy = two_vertex(1.0)
+    with pytest.raises(Exception):
+        oracle.forces(g, xy, a=4)
