@@ -72,12 +72,18 @@ typedef struct bl_server bl_server;
  * strength of repulsion. repulse_neighbors = 0 (default) repels non-adjacent
  * pairs only, as the combined force f(i,c) states; 1 repels every pair j != i,
  * as Algorithm S5's tree repulsion does literally. kahan: 1 = compensated FP32
- * repulsion sums, 0 = plain, -1 = automatic (on for n >= 2^20). */
+ * repulsion sums, 0 = plain, -1 = automatic (on for n >= 2^20). energy_model
+ * picks the (a,r)-energy model, attraction |c_i - c_j|^a / K with repulsion
+ * R K^2 / |c_i - c_j| (r = -1): BL_MODEL_FR (a = 2, Fruchterman-Reingold, the
+ * default and the paper's reported model), BL_MODEL_FA (a = 1, ForceAtlas),
+ * BL_MODEL_LINLOG (a = 0) or BL_MODEL_A3 (a = 3). */
+typedef enum { BL_MODEL_FR = 0, BL_MODEL_FA = 1, BL_MODEL_LINLOG = 2, BL_MODEL_A3 = 3 } bl_energy_model;
 typedef struct {
     float K;
     float R;
     int32_t repulse_neighbors;
     int32_t kahan;
+    int32_t energy_model;   /* bl_energy_model; 0 = Fruchterman-Reingold */
 } bl_force_params;
 
 typedef struct {

@@ -22,6 +22,9 @@ BL_OK, BL_EINVAL, BL_ENOMEM, BL_EBUDGET, BL_ECUDA, BL_ETIMEOUT, BL_EBUSY, BL_ENO
 STATUS_NAMES = ["BL_OK", "BL_EINVAL", "BL_ENOMEM", "BL_EBUDGET", "BL_ECUDA", "BL_ETIMEOUT",
                 "BL_EBUSY", "BL_ENOTREADY", "BL_ECANCELED"]
 MODES = {"exact": 0, "bh": 1, "auto": 2}
+# (a,r)-energy models: attraction d^a / K, repulsion R K^2 / d
+ENERGY_MODELS = {"fr": 0, "fa": 1, "linlog": 2, "a3": 3}
+MODEL_EXPONENT = {"fr": 2, "fa": 1, "linlog": 0, "a3": 3}
 CSR_SYMMETRIZE, CSR_DEDUP, CSR_SORT = 1, 2, 4
 THETA_DEFAULT = 1.2   # Section 4.1: the MAC threshold used with ForceAtlas2BH
 
@@ -35,7 +38,8 @@ class BatchLayoutError(RuntimeError):
 
 class ForceParams(ctypes.Structure):
     _fields_ = [("K", ctypes.c_float), ("R", ctypes.c_float),
-                ("repulse_neighbors", ctypes.c_int32), ("kahan", ctypes.c_int32)]
+                ("repulse_neighbors", ctypes.c_int32), ("kahan", ctypes.c_int32),
+                ("energy_model", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -211,13 +215,14 @@ class Layout:
     """Layout state of one graph (bl_layout)."""
 
     def __init__(self, graph: Graph, xy=None, seed: int = 0, start_iter: int = 0, K: float = 1.0,
-                 R: float = 1.0, repulse_neighbors: bool = False, kahan: int = -1, _handle=None):
+                 R: float = 1.0, repulse_neighbors: bool = False, kahan: int = -1, model: str = "fr",
+                 _handle=None):
         lib = load()
         self.graph = graph
         if _handle is not None:
             self._h = _handle
             return
-        prm = ForceParams(K, R, int(repulse_neighbors), int(kahan))
+        prm = ForceParams(K, R, int(repulse_neighbors), int(kahan), ENERGY_MODELS[model])
         h = ctypes.c_void_p()
         arr = None
         if xy is not None:
@@ -327,9 +332,9 @@ class Layout:
 
 
 def greedy_layout(graph: Graph, v0: int = -1, seed: int = 0, K: float = 1.0, R: float = 1.0,
-                  repulse_neighbors: bool = False) -> Layout:
+                  repulse_neighbors: bool = False, model: str = "fr") -> Layout:
     """A layout initialised by the greedy placement (bl_layout_init_greedy)."""
-    prm = ForceParams(K, R, int(repulse_neighbors), -1)
+    prm = ForceParams(K, R, int(repulse_neighbors), -1, ENERGY_MODELS[model])
     h = ctypes.c_void_p()
     _check(load().bl_layout_init_greedy(graph.handle, int(v0), ctypes.c_uint64(seed), ctypes.byref(prm),
                                         ctypes.byref(h)))
@@ -338,12 +343,12 @@ def greedy_layout(graph: Graph, v0: int = -1, seed: int = 0, K: float = 1.0, R: 
 
 def layout_run_noalloc(n: int, d_rowptr: int, d_colids: int, d_xy: int, iters: int, batch: int = 256,
                        K: float = 1.0, R: float = 1.0, repulse_neighbors: bool = False,
-                       start_iter: int = 0, d_energy: int = 0, stream: int = 0) -> None:
+                       start_iter: int = 0, d_energy: int = 0, stream: int = 0, model: str = "fr") -> None:
     """bl_layout_run_noalloc on device buffers the caller owns (raw device
     addresses): for callers that cannot allocate device memory. The library
     keeps its working memory in a fixed device array; calls that overlap on the
     GPU race on it."""
-    prm = ForceParams(K, R, int(repulse_neighbors), -1)
+    prm = ForceParams(K, R, int(repulse_neighbors), -1, ENERGY_MODELS[model])
     _check(load().bl_layout_run_noalloc(int(n), d_rowptr, d_colids, d_xy, int(iters), int(batch),
                                         ctypes.byref(prm), int(start_iter), d_energy or None,
                                         stream or None))

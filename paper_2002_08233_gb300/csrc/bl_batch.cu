@@ -41,6 +41,7 @@ struct BatchItem {
     double step0;         // Step at the first iteration of this launch
     int n, BS, iters, rn;
     float invK, negRK2;
+    int am;               // attraction exponent a of the (a,-1) model
 };
 
 struct BatchArgs {
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(T, (768 / T > 0 ? 768 / T : 1)) batch_kernel(B
                         if (valid) {
                             const int e1 = s_rp[i + 1];
                             for (int e = s_rp[i] + k; e < e1; e += 4)
-                                edge_terms(me.x, me.y, spos(sp, __ldg(&g.colids[e])), g.invK, g.rn != 0,
+                                edge_terms(me.x, me.y, spos(sp, __ldg(&g.colids[e])), g.invK, g.am, g.rn != 0,
                                            ax, ay, qx, qy);
                         }
 #pragma unroll
@@ -426,6 +427,7 @@ bl_status batch_launch(const BatchJob* jobs, int count, int chunk, cudaStream_t 
             it.rn = L->prm.repulse_neighbors;
             it.invK = 1.0f / L->prm.K;
             it.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
+            it.am = model_exponent(L->prm.energy_model);
             items.push_back(it);
         }
     }

@@ -571,7 +571,7 @@ __global__ void nbr_correct_kernel(const int* __restrict__ rowptr, const int* __
 // snapshot forces: ct_i = attraction at S + (-R K^2) rep_i (warp per row)
 __global__ void bh_snapshot_force_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
                                          const float2* __restrict__ S, int n, const float2* __restrict__ rep,
-                                         float invK, float negRK2, float2* __restrict__ out) {
+                                         float invK, int am, float negRK2, float2* __restrict__ out) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -582,7 +582,7 @@ __global__ void bh_snapshot_force_kernel(const int* __restrict__ rowptr, const i
         const float2 p = S[colids[e]];
         const float dx = p.x - me.x, dy = p.y - me.y;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-        const float a = d2 * rsqrt_sfu(d2) * invK;
+        const float a = attr_scale(d2, am) * invK;
         ax = fmaf(dx, a, ax);
         ay = fmaf(dy, a, ay);
     }
@@ -604,10 +604,10 @@ __global__ void bh_snapshot_force_kernel(const int* __restrict__ rowptr, const i
 // rows with more than kBigRow edges get a whole block from edge_pass_big_kernel).
 constexpr int kBigRow = 8192;
 
-__device__ __forceinline__ void attr_term(float2 me, float2 p, float invK, float& ax, float& ay) {
+__device__ __forceinline__ void attr_term(float2 me, float2 p, float invK, int am, float& ax, float& ay) {
     const float dx = p.x - me.x, dy = p.y - me.y;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-    const float sc = d2 * rsqrt_sfu(d2) * invK;
+    const float sc = attr_scale(d2, am) * invK;
     ax = fmaf(dx, sc, ax);
     ay = fmaf(dy, sc, ay);
 }
@@ -620,7 +620,7 @@ __device__ __forceinline__ void attr_term(float2 me, float2 p, float invK, float
 __device__ __forceinline__ void edge_terms_strided(const int* __restrict__ colids,
                                                    const float2* __restrict__ S, float2 me, int e0,
                                                    int e1, int es, int start, int stride, float invK,
-                                                   bool rn, float& ax, float& ay, float& qx, float& qy) {
+                                                   int am, bool rn, float& ax, float& ay, float& qx, float& qy) {
     for (int e = e0 + start; e < e1; e += 4 * stride) {
         int j[4];
         float2 p[4];
@@ -631,7 +631,7 @@ __device__ __forceinline__ void edge_terms_strided(const int* __restrict__ colid
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (j[k] < 0) continue;
-            if (e + k * stride >= es) attr_term(me, p[k], invK, ax, ay);
+            if (e + k * stride >= es) attr_term(me, p[k], invK, am, ax, ay);
             if (!rn) rep_pair(me.x, me.y, p[k].x, p[k].y, qx, qy);
         }
     }
@@ -639,7 +639,8 @@ __device__ __forceinline__ void edge_terms_strided(const int* __restrict__ colid
 
 __global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
                                  const int* __restrict__ split, const float2* __restrict__ S, int n,
-                                 float invK, int rn, float2* __restrict__ old, float2* __restrict__ rep) {
+                                 float invK, int am, int rn, float2* __restrict__ old,
+                                 float2* __restrict__ rep) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -648,7 +649,7 @@ __global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __re
     if (e1 - e0 > kBigRow) return;   // edge_pass_big_kernel
     const float2 me = S[i];
     float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
-    edge_terms_strided(colids, S, me, e0, e1, split[i], lane, 32, invK, rn != 0, ax, ay, qx, qy);
+    edge_terms_strided(colids, S, me, e0, e1, split[i], lane, 32, invK, am, rn != 0, ax, ay, qx, qy);
     ax = warp_sum(ax);
     ay = warp_sum(ay);
     if (!rn) {
@@ -666,7 +667,7 @@ __global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __re
 
 __global__ void __launch_bounds__(1024) edge_pass_big_kernel(
     const int* __restrict__ rowptr, const int* __restrict__ colids, const int* __restrict__ split,
-    const float2* __restrict__ S, const int* __restrict__ big_rows, float invK, int rn,
+    const float2* __restrict__ S, const int* __restrict__ big_rows, float invK, int am, int rn,
     float2* __restrict__ old, float2* __restrict__ rep) {
     __shared__ float4 s_w[32];
     const int i = big_rows[blockIdx.x];
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(1024) edge_pass_big_kernel(
     const float2 me = S[i];
     float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
     edge_terms_strided(colids, S, me, rowptr[i], rowptr[i + 1], split[i], threadIdx.x, blockDim.x, invK,
-                       rn != 0, ax, ay, qx, qy);
+                       am, rn != 0, ax, ay, qx, qy);
     ax = warp_sum(ax);
     ay = warp_sum(ay);
     qx = warp_sum(qx);
@@ -722,6 +723,7 @@ struct SweepArgs {
     int* status;
     int nlevels;
     int first_level;         // levels before it are done by level0_kernel
+    int am;                  // attraction exponent a of the (a,-1) model
     float invK, negRK2, stepf;
     unsigned long long* trace;   // optional: start time of each level (CTA 0)
 };
@@ -857,7 +859,7 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
         if (!gather_wait(a, g, lane)) return false;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (g.j[k] >= 0) attr_term(me, unpack_pos(g.v[k]), a.invK, sx, sy);
+            if (g.j[k] >= 0) attr_term(me, unpack_pos(g.v[k]), a.invK, a.am, sx, sy);
         e += 128;
         if (!__any_sync(0xffffffffu, e < p.tk.z)) break;
 #pragma unroll
@@ -1146,13 +1148,14 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         // one pass over the edges: attraction from neighbours that have not moved
         // yet, all rows at once, and the neighbour correction of the tree repulsion
         const int rn = L->prm.repulse_neighbors;
+        const int am = model_exponent(L->prm.energy_model);
         edge_pass_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
-            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, rn,
-            s->old.as<float2>(), s->rep.as<float2>());
+            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
+            rn, s->old.as<float2>(), s->rep.as<float2>());
         if (s->nbig > 0)
             edge_pass_big_kernel<<<s->nbig, 1024, 0, st>>>(L->g->rowptr.as<int>(), L->g->colids.as<int>(),
                                                            s->split.as<int>(), S, s->bigrows.as<int>(),
-                                                           1.0f / L->prm.K, rn, s->old.as<float2>(),
+                                                           1.0f / L->prm.K, am, rn, s->old.as<float2>(),
                                                            s->rep.as<float2>());
         BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, st));
         BL_TRY(layout_reset_sync_words(L, st));
@@ -1172,6 +1175,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         a.status = static_cast<int*>(L->status.p);
         a.nlevels = s->nlevels;
         a.invK = 1.0f / L->prm.K;
+        a.am = am;
         a.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
         a.stepf = (float)step;
         a.trace = nullptr;
@@ -1214,7 +1218,7 @@ bl_status bh_debug_forces(bl_layout* L, float theta, float2* f_out, cudaStream_t
     BL_TRY(bh_repulsion(L, S, theta, st));
     bh_snapshot_force_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
         L->g->rowptr.as<int>(), L->g->colids.as<int>(), S, n, L->bh->rep.as<float2>(), 1.0f / L->prm.K,
-        -L->prm.R * L->prm.K * L->prm.K, f_out);
+        model_exponent(L->prm.energy_model), -L->prm.R * L->prm.K * L->prm.K, f_out);
     BL_CUDA_TRY(cudaGetLastError());
     unsigned long long c[2] = {0, 0};
     BL_CUDA_TRY(cudaMemcpyAsync(c, L->bh->walkcnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     const bool snapshot = tk.iters == 0;
     const bool rn = prm.repulse_neighbors != 0;
     const float invK = prm.invK, negRK2 = prm.negRK2;
+    const int am = prm.am;
     float2* const buf0 = tk.pos;
     float2* const buf1 = tk.pos_alt;
 
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 const float2 me = s_pos[li];
                 float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
                 for (int ee = e0 + lane; ee < e1; ee += 32)
-                    edge_terms(me.x, me.y, nbr_pos(c0 + r, ee, e0), invK, rn, ax, ay, qx, qy);
+                    edge_terms(me.x, me.y, nbr_pos(c0 + r, ee, e0), invK, am, rn, ax, ay, qx, qy);
                 ax = warp_sum(ax);
                 ay = warp_sum(ay);
                 qx = warp_sum(qx);
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 if (e1 - e0 <= 32) {
                     const float2 me = s_pos[li];
                     for (int ee = e0 + gl; ee < e1; ee += W)
-                        edge_terms(me.x, me.y, nbr_pos(c0 + g, ee, e0), invK, rn, ax, ay, qx, qy);
+                        edge_terms(me.x, me.y, nbr_pos(c0 + g, ee, e0), invK, am, rn, ax, ay, qx, qy);
                 }
             }
             for (int o = W >> 1; o > 0; o >>= 1) {

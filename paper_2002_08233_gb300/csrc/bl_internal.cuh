@@ -86,7 +86,7 @@ void bh_state_free(BHState* s);
 
 struct bl_layout {
     const bl_graph* g = nullptr;
-    bl_force_params prm{1.0f, 1.0f, 0, -1};
+    bl_force_params prm{1.0f, 1.0f, 0, -1, BL_MODEL_FR};
     int64_t t = 0;                      // iterations done
     bl::DevBuf pos;                     // float2[n] live positions
     bl::DevBuf pos2;                    // float2[n] second buffer (BH sweep)
@@ -137,6 +137,7 @@ struct ExactParams {
     float invK;          // 1/K
     float negRK2;        // -R K^2
     int repulse_neighbors;
+    int am;              // attraction exponent a of the (a,-1) model
     int* status;         // device status word
     unsigned* bar;       // step counter (one arrival per CTA per step)
 };
@@ -164,6 +165,12 @@ bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, 
 
 // Barnes-Hut iterations of one layout (bl_bh.cu); the caller updates L's counters.
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st);
+
+// Attraction exponent a of an energy model (bl_energy_model): FR 2, FA 1, LinLog 0, A3 3.
+inline int model_exponent(int energy_model) {
+    static const int kA[4] = {2, 1, 0, 3};
+    return (energy_model >= 0 && energy_model < 4) ? kA[energy_model] : 2;
+}
 
 // Whole-GPU exact run of one layout (bl_runtime.cu); the caller updates L's counters.
 bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_out, cudaStream_t st);
@@ -317,15 +324,27 @@ struct GridBarrier {
     }
 };
 
-// CSR terms of one neighbour: attraction (d^2/K) (c_j - c_i)/d = (d/K)(c_j - c_i),
+// The attraction of the (a,-1)-energy model along c_j - c_i: |d|^a / K times the
+// unit vector = d^(a-1) / K (c_j - c_i). attr_scale(d2, a) = d^(a-1) from the
+// squared distance (BL_EPS2 included, so a coincident pair gives 0).
+__device__ __forceinline__ float attr_scale(float d2, int am) {
+    switch (am) {
+        case 2: return d2 * rsqrt_sfu(d2);   // d (Fruchterman-Reingold)
+        case 1: return 1.0f;                 // ForceAtlas
+        case 0: return rsqrt_sfu(d2);        // 1/d (LinLog)
+        default: return d2;                  // a = 3: d^2
+    }
+}
+
+// CSR terms of one neighbour: attraction d^(a-1)/K (c_j - c_i) (a = 2: (d/K)(c_j - c_i)),
 // and, unless repulse_neighbors, the repulsion term the all-pairs sum gave this
 // neighbour, computed with exactly rep_pair's expressions so that it cancels.
-__device__ __forceinline__ void edge_terms(float xi, float yi, float2 p, float invK, bool rn,
+__device__ __forceinline__ void edge_terms(float xi, float yi, float2 p, float invK, int am, bool rn,
                                            float& ax, float& ay, float& qx, float& qy) {
     const float dx = p.x - xi;
     const float dy = p.y - yi;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-    const float a = d2 * rsqrt_sfu(d2) * invK;
+    const float a = attr_scale(d2, am) * invK;
     ax = fmaf(dx, a, ax);
     ay = fmaf(dy, a, ay);
     if (!rn) {

@@ -66,10 +66,12 @@ extern "C" bl_status bl_layout_run_noalloc(int32_t n, const int32_t* d_rowptr, c
     if (iters < 0 || start_iter < 0) return set_error(BL_EINVAL, "bl_layout_run_noalloc: negative count");
     if (batch < 1 || batch > kMaxBatch)
         return set_error(BL_EINVAL, "bl_layout_run_noalloc: batch must be in [1, 8192]");
-    bl_force_params p{1.0f, 1.0f, 0, -1};
+    bl_force_params p{1.0f, 1.0f, 0, -1, BL_MODEL_FR};
     if (params) p = *params;
     if (!(p.K > 0.0f) || !(p.R > 0.0f))
         return set_error(BL_EINVAL, "bl_layout_run_noalloc: K and R must be positive");
+    if (p.energy_model < 0 || p.energy_model > 3)
+        return set_error(BL_EINVAL, "bl_layout_run_noalloc: energy_model must be 0..3");
     if (iters == 0) return BL_OK;
     ExactPlan plan;
     BL_TRY(exact_plan(n, batch, 0, 0, &plan));
@@ -102,6 +104,7 @@ extern "C" bl_status bl_layout_run_noalloc(int32_t n, const int32_t* d_rowptr, c
     prm.invK = 1.0f / p.K;
     prm.negRK2 = -p.R * p.K * p.K;
     prm.repulse_neighbors = p.repulse_neighbors;
+    prm.am = model_exponent(p.energy_model);
     prm.status = reinterpret_cast<int*>(sc);
     prm.bar = reinterpret_cast<unsigned*>(sc + 64);
     BL_TRY(exact_launch(plan, tk, prm, st));

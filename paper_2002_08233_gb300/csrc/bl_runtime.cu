@@ -175,6 +175,7 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     prm.invK = 1.0f / L->prm.K;
     prm.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
     prm.repulse_neighbors = L->prm.repulse_neighbors;
+    prm.am = model_exponent(L->prm.energy_model);
     prm.status = static_cast<int*>(L->status.p);
     prm.bar = layout_barrier_word(L);
     BL_TRY(layout_reset_sync_words(L, st));
@@ -196,10 +197,12 @@ bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64
     *out = nullptr;
     if (!g) return set_error(BL_EINVAL, "bl_layout_init: NULL graph");
     if (start_iter < 0) return set_error(BL_EINVAL, "bl_layout_init: start_iter < 0");
-    bl_force_params p{1.0f, 1.0f, 0, -1};
+    bl_force_params p{1.0f, 1.0f, 0, -1, BL_MODEL_FR};
     if (params) p = *params;
     if (!(p.K > 0.0f) || !(p.R > 0.0f) || !std::isfinite(p.K) || !std::isfinite(p.R))
         return set_error(BL_EINVAL, "bl_layout_init: K and R must be positive and finite");
+    if (p.energy_model < 0 || p.energy_model > 3)
+        return set_error(BL_EINVAL, "bl_layout_init: energy_model must be 0..3");
     bl_layout* L = new bl_layout();
     L->g = g;
     L->prm = p;
