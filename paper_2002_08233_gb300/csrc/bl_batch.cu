@@ -293,8 +293,8 @@ bl_status launch_shape(int shape, int ncap, const BatchItem* items, int nitems, 
     return BL_OK;
 }
 
-// Times every shape on a copy of (a sample of) the work and keeps the fastest for
-// this carve-out class. Positions of the real layouts are not touched.
+// Times every shape on a copy of the work (10 iterations) and keeps the fastest
+// for this carve-out class. Positions of the real layouts are not touched.
 bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator& al, cudaStream_t st,
                    int* shape_out) {
     int dev = 0;
@@ -315,9 +315,11 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
             return BL_OK;
         }
     }
-    // sample: every k-th graph of the largest-first list, about two per SM
-    const int want = std::max(1, 2 * device_sm_count());
-    const int stride = std::max<int>(1, (int)work.size() / want);
+    // the whole work list up to 8,192 graphs (every k-th beyond): the shapes
+    // differ in how many CTAs share an SM, which only shows when the launch has
+    // enough graphs to fill every CTA slot several times
+    const int want = 8192;
+    const int stride = std::max<int>(1, (int)((work.size() + want - 1) / want));
     std::vector<BatchItem> smp;
     size_t pos_floats = 0;
     for (size_t k = 0; k < work.size(); k += stride) {
@@ -326,7 +328,7 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
     }
     DevBuf pos, en, items, cur;
     BL_TRY(pos.ensure(al, pos_floats * sizeof(float)));
-    BL_TRY(en.ensure(al, smp.size() * 2 * sizeof(double)));
+    BL_TRY(en.ensure(al, smp.size() * 10 * sizeof(double)));
     BL_TRY(items.ensure(al, smp.size() * sizeof(BatchItem)));
     BL_TRY(cur.ensure(al, 16));
     size_t off = 0;
@@ -335,8 +337,8 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
         BL_CUDA_TRY(cudaMemcpyAsync(dst, smp[k].pos, (size_t)smp[k].n * sizeof(float2),
                                     cudaMemcpyDeviceToDevice, st));
         smp[k].pos = dst;
-        smp[k].energy = en.as<double>() + 2 * k;
-        smp[k].iters = std::min(smp[k].iters, 2);
+        smp[k].energy = en.as<double>() + 10 * k;
+        smp[k].iters = std::min(smp[k].iters, 10);
         off += 2 * (size_t)smp[k].n;
     }
     BL_CUDA_TRY(cudaMemcpyAsync(items.p, smp.data(), smp.size() * sizeof(BatchItem),

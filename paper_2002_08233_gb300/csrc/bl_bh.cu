@@ -212,14 +212,23 @@ __global__ void bbox_partial_kernel(const float2* __restrict__ pos, int n, float
 // box[0] = xmin, box[1] = ymin, box[2] = D, box[3] = 65536/D (0 when the box is
 // degenerate: every code is then 0), box[4 + l] = (D * 2^-l)^2 for l = 0..16
 __global__ void bbox_final_kernel(const float4* __restrict__ part, int nb, float* __restrict__ box) {
-    if (threadIdx.x != 0) return;
-    float4 r = part[0];
-    for (int b = 1; b < nb; b++) {
-        r.x = fminf(r.x, part[b].x);
-        r.y = fmaxf(r.y, part[b].y);
-        r.z = fminf(r.z, part[b].z);
-        r.w = fmaxf(r.w, part[b].w);
+    // one warp: min and max are exact, so the order of the reduction is free
+    const int lane = threadIdx.x;
+    float4 r = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    for (int b = lane; b < nb; b += 32) {
+        const float4 p = part[b];
+        r.x = fminf(r.x, p.x);
+        r.y = fmaxf(r.y, p.y);
+        r.z = fminf(r.z, p.z);
+        r.w = fmaxf(r.w, p.w);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        r.x = fminf(r.x, __shfl_xor_sync(0xffffffffu, r.x, o));
+        r.y = fmaxf(r.y, __shfl_xor_sync(0xffffffffu, r.y, o));
+        r.z = fminf(r.z, __shfl_xor_sync(0xffffffffu, r.z, o));
+        r.w = fmaxf(r.w, __shfl_xor_sync(0xffffffffu, r.w, o));
+    }
+    if (lane != 0) return;
     const float dxr = __fsub_rn(r.y, r.x), dyr = __fsub_rn(r.w, r.z);
     const float D = dxr > dyr ? dxr : dyr;
     box[0] = r.x;
