@@ -315,6 +315,12 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
             return BL_OK;
         }
     }
+    // too few graphs to tell the shapes apart (they differ in how CTAs share an
+    // SM): the shape measured best on a large mix, not remembered
+    if ((int)work.size() < 4 * device_sm_count()) {
+        *shape_out = 0;
+        return BL_OK;
+    }
     // the whole work list up to 8,192 graphs (every k-th beyond): the shapes
     // differ in how many CTAs share an SM, which only shows when the launch has
     // enough graphs to fill every CTA slot several times
