@@ -172,3 +172,18 @@ def test_invalid_arguments(core):
     sd = np.zeros(1, dtype=np.uint64)
     outs = (ctypes.c_void_p * 1)()
     assert lib.bl_layout_batch(hs, 1, sd.ctypes.data, 1, 0, 0, 1.2, outs) == 1
+
+
+def test_full_mix_sampled_parity(core):
+    """The bench's batched workload at full size (4,096 graphs, n log-uniform in
+    [50, 5,000], minibatch 64) in one launch; an even sample of 12 graphs after
+    one iteration against the oracle."""
+    gs = synth.small_graph_mix(count=4096, seed=4)
+    seeds = np.arange(len(gs), dtype=np.uint64)
+    _, Ls = _batch(core, gs, seeds, 1, 64)
+    for k in np.linspace(0, len(gs) - 1, 12).astype(int):
+        g = gs[k]
+        xy = synth.uniform_positions(g.n, int(seeds[k]))
+        xr, sens = oracle_sensitivity(g, xy, 1, 64, trials=1, nthreads=NCPU)
+        err = position_error(Ls[k].positions(), xr)
+        assert err <= position_tolerance(TOL_POS_EXACT, sens), (k, g.n, err, sens)

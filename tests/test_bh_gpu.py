@@ -179,3 +179,15 @@ def test_rmat20_sampled_forces(core, rmat20):
     ref, mag = oracle.forces(g, xy.astype(np.float64), mode=oracle.BH, theta=1.2, lo=0, hi=256,
                              nthreads=NCPU)
     assert force_error(f[:256], ref, mag).max() <= TOL_FORCE_BH
+
+
+def test_rmat20_one_iteration_positions(core, rmat20):
+    """The bench's R-MAT scale-20 workload, one whole iteration (tree, walk,
+    edge pass, dataflow sweep) against the oracle's Algorithm S5 iteration."""
+    g = rmat20
+    xy = synth.uniform_positions(g.n, 0)
+    _, L = _layout(core, g, xy)
+    L.run(1, 256, "bh", 1.2)
+    xr, sens = oracle_sensitivity(g, xy, 1, 256, trials=1, mode=oracle.BH, theta=1.2, nthreads=NCPU)
+    err = position_error(L.positions(), xr)
+    assert err <= position_tolerance(TOL_POS_BH, sens), (err, sens)
