@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libbatchlayout.so")
 SOURCES = ["bl_runtime.cu", "bl_exact.cu", "bl_bh.cu", "bl_quality.cu", "bl_serve.cu",
-           "bl_noalloc.cu", "bl_batch.cu", "bl_debug.cu"]
+           "bl_noalloc.cu", "bl_batch.cu", "bl_debug.cu",
+           "bl_exact_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")

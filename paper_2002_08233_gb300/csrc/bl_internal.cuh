@@ -172,6 +172,16 @@ inline int model_exponent(int energy_model) {
     return (energy_model >= 0 && energy_model < 4) ? kA[energy_model] : 2;
 }
 
+// Exact mode on one thread-block cluster for small graphs (bl_exact_cluster.cu).
+constexpr int kClusterMaxN = 8192;
+constexpr int kClusterAutoN = 3072;   // measured crossover to the whole-GPU engine (n ~ 3,000)
+bool cluster_engine_fits(int n, int BS, int64_t nnz);
+// `iters` iterations of positions pos (updated in place); e_iter_buf holds
+// iters x 16 doubles; energy (may be null) receives the per-iteration energies.
+bl_status cluster_run(const int* rowptr, const int* colids, int64_t nnz, int n, float2* pos, int iters, int BS,
+                      double step0, float invK, float negRK2, int rn, int am, double* e_iter_buf,
+                      double* energy, cudaStream_t st, int* C_out);
+
 // Whole-GPU exact run of one layout (bl_runtime.cu); the caller updates L's counters.
 bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_out, cudaStream_t st);
 

@@ -136,9 +136,28 @@ static bool use_kahan(const bl_layout* L) {
     return L->prm.kahan > 0 || (L->prm.kahan < 0 && L->g->n >= (1 << 20));
 }
 
+// Small graphs whose minibatch chain dominates run on one thread-block cluster
+// (BL_EXACT_ENGINE=grid|cluster forces an engine).
+static bool use_cluster_engine(const bl_layout* L, int BS) {
+    const int n = L->g->n;
+    if (!cluster_engine_fits(n, BS, L->g->nnz)) return false;
+    if (const char* e = std::getenv("BL_EXACT_ENGINE")) return e[0] == 'c';
+    return n <= kClusterAutoN;
+}
+
 bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_out,
                     cudaStream_t st) {
     const int n = L->g->n;
+    if (!snapshot && iters > 0 && use_cluster_engine(L, BS)) {
+        double s = 1.0;
+        for (int64_t k = 0; k < L->t; k++) s *= 0.999;
+        BL_TRY(L->epart.ensure(L->alloc, (size_t)iters * 16 * sizeof(double)));
+        BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(iters, 1) * sizeof(double)));
+        return cluster_run(L->g->rowptr.as<int>(), L->g->colids.as<int>(), L->g->nnz, n, L->pos.as<float2>(),
+                           iters, BS, s, 1.0f / L->prm.K, -L->prm.R * L->prm.K * L->prm.K,
+                           L->prm.repulse_neighbors, model_exponent(L->prm.energy_model),
+                           L->epart.as<double>(), L->energy.as<double>(), st, nullptr);
+    }
     ExactPlan plan;
     BL_TRY(exact_plan(n, BS, 0, 0, &plan));
     ExactTask tk{};

@@ -37,7 +37,7 @@ def test_noalloc_matches_layout_run_twice(core):
     import torch
     lib = core.load()
     fn = _noalloc_fn(lib)
-    g = synth.erdos_renyi(3000, 6.0, 21)
+    g = synth.erdos_renyi(4000, 6.0, 21)   # above the cluster engine's size: both calls run the whole-GPU engine
     xy = synth.uniform_positions(g.n, 21)
     # existing entry point
     G = core.Graph(g)
