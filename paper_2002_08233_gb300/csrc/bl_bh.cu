@@ -67,8 +67,8 @@ struct BHState {
     DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
     DevBuf walkcnt;                     // unsigned long long[2]: far nodes, near pairs
     // sweep
-    int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, lvl0_rows = 0;
-    DevBuf split, bigrows, old;         // row split points, rows with many old edges, old attraction
+    int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, nmid = 0, lvl0_rows = 0;
+    DevBuf split, bigrows, midrows, old;   // row split points, long and medium rows, old attraction
     DevBuf lvl_ptr, tasks, seg_off, seg_sum, seg_cnt;   // level-set schedule
     DevBuf e_row, epart;                // per-row |ct|^2, reduction partials
 };
@@ -78,7 +78,7 @@ void bh_state_free(BHState* s) {
     DevBuf* bufs[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->hist, &s->scan_part,
                       &s->bpart, &s->box, &s->cnt, &s->spos, &s->nd_first, &s->nd_count,
                       &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
-                      &s->lvl_nodes, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->old,
+                      &s->lvl_nodes, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->midrows, &s->old,
                       &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->seg_cnt, &s->e_row,
                       &s->epart};
     for (DevBuf* b : bufs) b->release();
@@ -646,32 +646,59 @@ __device__ __forceinline__ void edge_terms_strided(const int* __restrict__ colid
     }
 }
 
+constexpr int kShortRow = 256;   // rows up to this many edges: 8 lanes each
+
+__device__ __forceinline__ void edge_pass_finish(int i, float ax, float ay, float qx, float qy, int rn,
+                                                 float2* __restrict__ old, float2* __restrict__ rep) {
+    old[i] = make_float2(ax, ay);
+    if (!rn) {
+        const float2 r = rep[i];
+        rep[i] = make_float2(r.x - qx, r.y - qy);
+    }
+}
+
+// Short rows (most of them): 8 lanes per row, 4 rows per warp.
 __global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
                                  const int* __restrict__ split, const float2* __restrict__ S, int n,
                                  float invK, int am, int rn, float2* __restrict__ old,
                                  float2* __restrict__ rep) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const int i = warp;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t >> 3, sub = t & 7;
+    const unsigned mask = 0xFFu << (threadIdx.x & 24);   // this row's 8 lanes
+    if (i >= n) return;   // whole 8-lane groups
     const int e0 = rowptr[i], e1 = rowptr[i + 1];
-    if (e1 - e0 > kBigRow) return;   // edge_pass_big_kernel
+    if (e1 - e0 > kShortRow) return;   // edge_pass_mid_kernel / edge_pass_big_kernel
     const float2 me = S[i];
     float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
-    edge_terms_strided(colids, S, me, e0, e1, split[i], lane, 32, invK, am, rn != 0, ax, ay, qx, qy);
+    edge_terms_strided(colids, S, me, e0, e1, split[i], sub, 8, invK, am, rn != 0, ax, ay, qx, qy);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(mask, ax, o);
+        ay += __shfl_xor_sync(mask, ay, o);
+        qx += __shfl_xor_sync(mask, qx, o);
+        qy += __shfl_xor_sync(mask, qy, o);
+    }
+    if (sub == 0) edge_pass_finish(i, ax, ay, qx, qy, rn, old, rep);
+}
+
+// Rows with more than kShortRow and at most kBigRow edges: a warp each.
+__global__ void edge_pass_mid_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
+                                     const int* __restrict__ split, const float2* __restrict__ S,
+                                     const int* __restrict__ mid_rows, int nmid, float invK, int am, int rn,
+                                     float2* __restrict__ old, float2* __restrict__ rep) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nmid) return;
+    const int i = mid_rows[w];
+    const float2 me = S[i];
+    float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
+    edge_terms_strided(colids, S, me, rowptr[i], rowptr[i + 1], split[i], lane, 32, invK, am, rn != 0, ax, ay,
+                       qx, qy);
     ax = warp_sum(ax);
     ay = warp_sum(ay);
-    if (!rn) {
-        qx = warp_sum(qx);
-        qy = warp_sum(qy);
-    }
-    if (lane == 0) {
-        old[i] = make_float2(ax, ay);
-        if (!rn) {
-            const float2 r = rep[i];
-            rep[i] = make_float2(r.x - qx, r.y - qy);
-        }
-    }
+    qx = warp_sum(qx);
+    qy = warp_sum(qy);
+    if (lane == 0) edge_pass_finish(i, ax, ay, qx, qy, rn, old, rep);
 }
 
 __global__ void __launch_bounds__(1024) edge_pass_big_kernel(
@@ -1069,13 +1096,14 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     const int n = g->n;
     const int* rp = g->h_rowptr.data();
     const int* ci = g->h_colids.data();
-    std::vector<int> split(n), level(n), bigrows;
+    std::vector<int> split(n), level(n), bigrows, midrows;
     int nlev = 0;
     for (int i = 0; i < n; i++) {
         const int lo = (i / BS) * BS;
         const int* sp = std::lower_bound(ci + rp[i], ci + rp[i + 1], lo);
         split[i] = (int)(sp - ci);
         if (rp[i + 1] - rp[i] > kBigRow) bigrows.push_back(i);   // edge_pass_big_kernel
+        else if (rp[i + 1] - rp[i] > kShortRow) midrows.push_back(i);   // edge_pass_mid_kernel
         int d = 0;
         for (const int* c = ci + rp[i]; c < sp; c++) d = std::max(d, level[*c]);
         level[i] = d + 1;
@@ -1117,6 +1145,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     };
     BL_TRY(up(s->split, split.data(), split.size() * 4));
     BL_TRY(up(s->bigrows, bigrows.data(), bigrows.size() * 4));
+    BL_TRY(up(s->midrows, midrows.data(), midrows.size() * 4));
     BL_TRY(up(s->lvl_ptr, lvl_ptr.data(), lvl_ptr.size() * 4));
     BL_TRY(up(s->tasks, tasks.data(), tasks.size() * sizeof(int4)));
     BL_TRY(up(s->seg_off, seg_off.data(), seg_off.size() * 4));
@@ -1127,6 +1156,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     BL_TRY(s->old.ensure(al, (size_t)n * sizeof(float2)));
     BL_CUDA_TRY(cudaStreamSynchronize(st));
     s->nbig = (int)bigrows.size();
+    s->nmid = (int)midrows.size();
     s->nlevels = nlev;
     s->plan_bs = BS;
     s->plan_seg = segE;
@@ -1158,9 +1188,13 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         // yet, all rows at once, and the neighbour correction of the tree repulsion
         const int rn = L->prm.repulse_neighbors;
         const int am = model_exponent(L->prm.energy_model);
-        edge_pass_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
+        edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, st>>>(
             L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
             rn, s->old.as<float2>(), s->rep.as<float2>());
+        if (s->nmid > 0)
+            edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, st>>>(
+                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->midrows.as<int>(),
+                s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->rep.as<float2>());
         if (s->nbig > 0)
             edge_pass_big_kernel<<<s->nbig, 1024, 0, st>>>(L->g->rowptr.as<int>(), L->g->colids.as<int>(),
                                                            s->split.as<int>(), S, s->bigrows.as<int>(),

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kClThreads, 1) exact_cluster_kernel(ClusterTas
                     const int slot = (b & 1) * BS + (i - r0);
                     for (int c = 0; c < C; c++) remote[c][slot] = np2;   // every CTA's inbox
                 }
-                __syncthreads();   // s_red is reused by the next group round
+                if (m0 + groups < mine) __syncthreads();   // s_red is reused by the next round
             }
             cl.sync();   // the minibatch's new positions are in every inbox
             for (int r = r0 + tid; r < r1; r += kClThreads) P[r] = box[r - r0];
