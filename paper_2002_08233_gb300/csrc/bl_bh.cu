@@ -69,8 +69,12 @@ struct BHState {
     // sweep
     int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, nmid = 0, lvl0_rows = 0;
     DevBuf split, bigrows, midrows, old;   // row split points, long and medium rows, old attraction
+    DevBuf corr;                        // float2[n]: exact repulsion of the CSR neighbours at S
     DevBuf lvl_ptr, tasks, seg_off, seg_sum, seg_cnt;   // level-set schedule
     DevBuf e_row, epart;                // per-row |ct|^2, reduction partials
+    // the edge pass runs on a side stream while the tree is built and walked
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 void bh_state_free(BHState* s) {
@@ -79,9 +83,13 @@ void bh_state_free(BHState* s) {
                       &s->bpart, &s->box, &s->cnt, &s->spos, &s->nd_first, &s->nd_count,
                       &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
                       &s->lvl_nodes, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->midrows, &s->old,
+                      &s->corr,
                       &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->seg_cnt, &s->e_row,
                       &s->epart};
     for (DevBuf* b : bufs) b->release();
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->side) cudaStreamDestroy(s->side);
     delete s;
 }
 
@@ -648,20 +656,20 @@ __device__ __forceinline__ void edge_terms_strided(const int* __restrict__ colid
 
 constexpr int kShortRow = 256;   // rows up to this many edges: 8 lanes each
 
-__device__ __forceinline__ void edge_pass_finish(int i, float ax, float ay, float qx, float qy, int rn,
-                                                 float2* __restrict__ old, float2* __restrict__ rep) {
+// old[i]: attraction from the neighbours that do not move before row i does;
+// corr[i]: exact repulsion of all of i's neighbours (zero when the tree's
+// repulsion keeps them), taken off the tree sum when the row is finished
+__device__ __forceinline__ void edge_pass_finish(int i, float ax, float ay, float qx, float qy,
+                                                 float2* __restrict__ old, float2* __restrict__ corr) {
     old[i] = make_float2(ax, ay);
-    if (!rn) {
-        const float2 r = rep[i];
-        rep[i] = make_float2(r.x - qx, r.y - qy);
-    }
+    corr[i] = make_float2(qx, qy);
 }
 
 // Short rows (most of them): 8 lanes per row, 4 rows per warp.
 __global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
                                  const int* __restrict__ split, const float2* __restrict__ S, int n,
                                  float invK, int am, int rn, float2* __restrict__ old,
-                                 float2* __restrict__ rep) {
+                                 float2* __restrict__ corr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t >> 3, sub = t & 7;
     const unsigned mask = 0xFFu << (threadIdx.x & 24);   // this row's 8 lanes
@@ -678,14 +686,14 @@ __global__ void edge_pass_kernel(const int* __restrict__ rowptr, const int* __re
         qx += __shfl_xor_sync(mask, qx, o);
         qy += __shfl_xor_sync(mask, qy, o);
     }
-    if (sub == 0) edge_pass_finish(i, ax, ay, qx, qy, rn, old, rep);
+    if (sub == 0) edge_pass_finish(i, ax, ay, qx, qy, old, corr);
 }
 
 // Rows with more than kShortRow and at most kBigRow edges: a warp each.
 __global__ void edge_pass_mid_kernel(const int* __restrict__ rowptr, const int* __restrict__ colids,
                                      const int* __restrict__ split, const float2* __restrict__ S,
                                      const int* __restrict__ mid_rows, int nmid, float invK, int am, int rn,
-                                     float2* __restrict__ old, float2* __restrict__ rep) {
+                                     float2* __restrict__ old, float2* __restrict__ corr) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nmid) return;
@@ -698,13 +706,13 @@ __global__ void edge_pass_mid_kernel(const int* __restrict__ rowptr, const int* 
     ay = warp_sum(ay);
     qx = warp_sum(qx);
     qy = warp_sum(qy);
-    if (lane == 0) edge_pass_finish(i, ax, ay, qx, qy, rn, old, rep);
+    if (lane == 0) edge_pass_finish(i, ax, ay, qx, qy, old, corr);
 }
 
 __global__ void __launch_bounds__(1024) edge_pass_big_kernel(
     const int* __restrict__ rowptr, const int* __restrict__ colids, const int* __restrict__ split,
     const float2* __restrict__ S, const int* __restrict__ big_rows, float invK, int am, int rn,
-    float2* __restrict__ old, float2* __restrict__ rep) {
+    float2* __restrict__ old, float2* __restrict__ corr) {
     __shared__ float4 s_w[32];
     const int i = big_rows[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -726,11 +734,7 @@ __global__ void __launch_bounds__(1024) edge_pass_big_kernel(
             t.z += s_w[w].z;
             t.w += s_w[w].w;
         }
-        old[i] = make_float2(t.x, t.y);
-        if (!rn) {
-            const float2 r = rep[i];
-            rep[i] = make_float2(r.x - t.z, r.y - t.w);
-        }
+        edge_pass_finish(i, t.x, t.y, t.z, t.w, old, corr);
     }
 }
 
@@ -748,7 +752,8 @@ struct SweepArgs {
     const int* colids;
     const float2* bold;      // positions at iteration start (S)
     float2* bnew;            // positions after this iteration's update
-    const float2* rep;       // repulsion sums (unscaled)
+    const float2* rep;       // repulsion sums of the tree walk (unscaled)
+    const float2* corr;      // their neighbour correction, rep - corr is the row's repulsion
     const float2* old;       // attraction from not-yet-moved neighbours
     const int* lvl_ptr;      // tasks of level l: [lvl_ptr[l], lvl_ptr[l+1])
     const int4* tasks;       // {row, first edge, end edge, segment | nseg << 16}
@@ -784,6 +789,12 @@ __device__ __forceinline__ unsigned long long read_pos(const float2* p) {
 }
 __device__ __forceinline__ float2 unpack_pos(unsigned long long v) {
     return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
+}
+
+// The row's repulsion sum: the tree's, less its CSR neighbours' exact terms.
+__device__ __forceinline__ float2 row_rep(const SweepArgs& a, int i) {
+    const float2 r = a.rep[i], q = a.corr[i];
+    return make_float2(__fsub_rn(r.x, q.x), __fsub_rn(r.y, q.y));
 }
 
 // The row's update: ct = attraction (this iteration's moved neighbours sx,sy +
@@ -823,7 +834,7 @@ __device__ __forceinline__ void task_prefetch(const SweepArgs& a, int t, int lan
     p.tk = a.tasks[t];
     const int i = p.tk.x;
     p.me = a.bold[i];
-    p.rp = a.rep[i];
+    p.rp = row_rep(a, i);
     p.od = a.old[i];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -838,7 +849,7 @@ __global__ void level0_kernel(SweepArgs a) {
     const int t1 = a.lvl_ptr[1];
     for (int t = a.lvl_ptr[0] + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         const int i = a.tasks[t].x;
-        finish_row(a, i, a.bold[i], a.rep[i], a.old[i], 0.f, 0.f);
+        finish_row(a, i, a.bold[i], row_rep(a, i), a.old[i], 0.f, 0.f);
     }
 }
 
@@ -984,6 +995,9 @@ static bl_status bh_ensure(bl_layout* L) {
     const int n = L->g->n;
     if (!L->bh) L->bh = new BHState();
     BHState* s = L->bh;
+    if (!s->side) BL_CUDA_TRY(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    if (!s->ev_fork) BL_CUDA_TRY(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+    if (!s->ev_join) BL_CUDA_TRY(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
     if (s->n == n && s->cap_nodes > 0) return BL_OK;
     const Allocator& al = L->alloc;
     const size_t N = (size_t)n;
@@ -1154,6 +1168,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     BL_TRY(s->e_row.ensure(al, (size_t)n * 8));
     BL_TRY(s->epart.ensure(al, 1024 * 8));
     BL_TRY(s->old.ensure(al, (size_t)n * sizeof(float2)));
+    BL_TRY(s->corr.ensure(al, (size_t)n * sizeof(float2)));
     BL_CUDA_TRY(cudaStreamSynchronize(st));
     s->nbig = (int)bigrows.size();
     s->nmid = (int)midrows.size();
@@ -1182,25 +1197,32 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
     for (int t = 0; t < iters; t++) {
         const float2* S = L->pos.as<float2>();
         float2* bnew = L->pos2.as<float2>();
-        BL_TRY(bh_build(L, S, st));
-        BL_TRY(bh_repulsion(L, S, theta, st, false));
-        // one pass over the edges: attraction from neighbours that have not moved
-        // yet, all rows at once, and the neighbour correction of the tree repulsion
+        // side stream: one pass over the edges (attraction from neighbours that
+        // have not moved yet, all rows at once, and the neighbour correction of
+        // the tree repulsion) and the sweep's resets; it needs only S and the
+        // graph, so it runs while the tree of S is built and walked
         const int rn = L->prm.repulse_neighbors;
         const int am = model_exponent(L->prm.energy_model);
-        edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, st>>>(
+        BL_CUDA_TRY(cudaEventRecord(s->ev_fork, st));
+        BL_CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, s->side>>>(
             L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
-            rn, s->old.as<float2>(), s->rep.as<float2>());
+            rn, s->old.as<float2>(), s->corr.as<float2>());
         if (s->nmid > 0)
-            edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, st>>>(
+            edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, s->side>>>(
                 L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->midrows.as<int>(),
-                s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->rep.as<float2>());
+                s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
         if (s->nbig > 0)
-            edge_pass_big_kernel<<<s->nbig, 1024, 0, st>>>(L->g->rowptr.as<int>(), L->g->colids.as<int>(),
-                                                           s->split.as<int>(), S, s->bigrows.as<int>(),
-                                                           1.0f / L->prm.K, am, rn, s->old.as<float2>(),
-                                                           s->rep.as<float2>());
-        BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, st));
+            edge_pass_big_kernel<<<s->nbig, 1024, 0, s->side>>>(
+                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
+                1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
+        BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
+        BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
+        BL_CUDA_TRY(cudaGetLastError());
+        BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
+        // main stream: the tree of S and its walk
+        BL_TRY(bh_build(L, S, st));
+        BL_TRY(bh_repulsion(L, S, theta, st, false));
         BL_TRY(layout_reset_sync_words(L, st));
         SweepArgs a{};
         a.rowptr = L->g->rowptr.as<int>();
@@ -1208,6 +1230,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         a.bold = S;
         a.bnew = bnew;
         a.rep = s->rep.as<float2>();
+        a.corr = s->corr.as<float2>();
         a.old = s->old.as<float2>();
         a.lvl_ptr = s->lvl_ptr.as<int>();
         a.tasks = s->tasks.as<int4>();
@@ -1230,7 +1253,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
             L->trace_count = s->nlevels + 1;
         }
         a.first_level = s->nlevels > 0 ? 1 : 0;
-        BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), st));   // every slot kUnset
+        BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
         if (a.first_level == 1) {
             const int n0 = s->lvl0_rows;
             level0_kernel<<<std::max(1, std::min(div_up(n0, 256), 8 * device_sm_count())), 256, 0, st>>>(a);
