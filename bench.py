@@ -261,7 +261,7 @@ def run_exact(args, rank, world, local):
                      "frac": achieved / peak_pairs,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch
                      # (10 iterations) of this kernel on this workload
-                     "traffic": 2962176, "traffic_unit": "bytes per launch",
+                     "traffic": 2963200, "traffic_unit": "bytes per launch",
                      "kernel": "exact_grid_kernel",
                      "peak_source": f"{SMS} SMs x {MUFU_PER_CLK_PER_SM} SFU lanes/clk x "
                                     f"{sm_max:.0f} MHz ({src} sm_max_mhz)"},
@@ -376,6 +376,9 @@ def run_bh(args, local, steps=5, warmup=2):
         "ms_per_iteration": total / steps, "steps": steps, "warmup": warmup,
         "n": n, "nnz": g.nnz,
         "tree_walk_far_nodes": st["bh_far_nodes"], "tree_walk_leaf_vertices": st["bh_near_pairs"],
+        # far-field nodes accepted plus leaf vertices met (each query's own excluded),
+        # per second of whole iteration
+        "interactions_per_s": (st["bh_far_nodes"] + st["bh_near_pairs"] - n) / (total / steps / 1e3),
         "l2": "working set > L2 (positions, sorted copies and a ~2n-node tree)",
     }
 
