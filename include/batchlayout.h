@@ -134,7 +134,6 @@ void bl_graph_free(bl_graph *g);
 bl_status bl_layout_init(const bl_graph *g, const float *xy, uint64_t seed, int64_t start_iter,
                          const bl_force_params *params, bl_layout **out);
 
-/* Replaces the positions (host, 2n floats) and the iteration counter. */
 /* Greedy initialisation (Section 3.6, Algorithm 3): a layout whose positions
  * come from a depth-first placement starting at v0 = (0, 0): each vertex U taken
  * from the stack puts its not yet placed neighbours, in CSR order, on the unit
@@ -146,6 +145,7 @@ bl_status bl_layout_init(const bl_graph *g, const float *xy, uint64_t seed, int6
 bl_status bl_layout_init_greedy(const bl_graph *g, int64_t v0, uint64_t seed,
                                 const bl_force_params *params, bl_layout **out);
 
+/* Replaces the positions (host, 2n floats) and the iteration counter. */
 bl_status bl_layout_set_positions(bl_layout *L, const float *xy, int64_t start_iter);
 
 /* Runs `iters` iterations with minibatch size `batch` (1 <= batch <= 8192)
@@ -153,7 +153,9 @@ bl_status bl_layout_set_positions(bl_layout *L, const float *xy, int64_t start_i
  * Algorithm 2 with Section 2.2's forces, Algorithm S5 for BL_BH. Continues the
  * step schedule from the layout's iteration counter; runs of k and m
  * iterations give the same positions and energies, bit for bit, as one run of
- * k + m. Synchronises; BL_ETIMEOUT if a bounded device-side wait gave up. */
+ * k + m. Synchronises; BL_ETIMEOUT if a bounded device-side wait gave up.
+ * BL_BH takes graphs of at most 126,322,567 vertices (its quadtree reserves
+ * 17 n + 1 nodes with 32-bit indices); larger ones give BL_EINVAL. */
 bl_status bl_layout_run(bl_layout *L, int32_t iters, int32_t batch, bl_mode mode, float theta);
 
 /* Runs at most max_iters iterations and stops after the first iteration whose
@@ -253,7 +255,8 @@ bl_status bl_server_create(size_t mem_budget_bytes, bl_server **out);
 /* Queues a layout of g (which must stay alive until polled) with seeded initial
  * positions (as bl_layout_init), `iters` iterations of minibatch `batch`. mode
  * BL_AUTO picks exact below 50,000 vertices and BH otherwise. BL_EBUDGET if the
- * request could never fit the budget. *ticket identifies the request. */
+ * request could never fit the budget; BL_EINVAL for a BH request over BH's
+ * vertex limit (bl_layout_run). *ticket identifies the request. */
 bl_status bl_serve_submit(bl_server *S, const bl_graph *g, uint64_t seed, int32_t iters,
                           int32_t batch, bl_mode mode, float theta, uint64_t *ticket);
 

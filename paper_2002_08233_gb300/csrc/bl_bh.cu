@@ -993,6 +993,8 @@ __global__ void energy_parts_kernel(const double* __restrict__ part, int np, dou
 
 static bl_status bh_ensure(bl_layout* L) {
     const int n = L->g->n;
+    if ((int64_t)n > kBHMaxN)
+        return set_error(BL_EINVAL, "Barnes-Hut mode: more vertices than the quadtree's 32-bit node indices allow");
     if (!L->bh) L->bh = new BHState();
     BHState* s = L->bh;
     if (!s->side) BL_CUDA_TRY(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));

@@ -199,6 +199,9 @@ bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64
 // ---------------------------------------------------------------------------
 
 constexpr int kBatchMaxN = 16384;   // largest graph one CTA holds in shared memory
+// Barnes-Hut: the quadtree reserves 17 n + 1 nodes (at most one per level and
+// sorted position, plus the root) and indexes them with int32
+constexpr int64_t kBHMaxN = (0x7fffffffLL - 1) / 17;
 constexpr int kBatchMaxBS = 256;    // largest minibatch of the batched kernel
 
 // Exact iterations of many layouts: graphs within the limits above go into one

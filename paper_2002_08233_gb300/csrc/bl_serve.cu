@@ -259,6 +259,8 @@ bl_status bl_serve_submit(bl_server* S, const bl_graph* g, uint64_t seed, int32_
         return set_error(BL_EINVAL, "bl_serve_submit: bad mode");
     if (mode == BL_AUTO) mode = g->n < kAutoExactBelow ? BL_EXACT : BL_BH;
     if (mode == BL_BH && !(theta >= 0.0f)) return set_error(BL_EINVAL, "bl_serve_submit: theta must be >= 0");
+    if (mode == BL_BH && (int64_t)g->n > kBHMaxN)
+        return set_error(BL_EINVAL, "bl_serve_submit: graph too large for Barnes-Hut mode");
     Job* j = new Job();
     j->g = g;
     j->seed = seed;

@@ -66,3 +66,24 @@ def test_server_request_fails_alone_on_allocation_error(core):
     assert st["completed"] == 1 and st["bytes"] == 0
     ref = core.layout_batch([G], [1], 20, 64)[0]
     assert np.array_equal(r[0], ref.positions())
+
+
+def test_bh_rejects_graphs_over_its_vertex_limit(core):
+    # one vertex over the quadtree's budget: 17 n + 1 nodes no longer fit int32
+    # indices, so both the run and a serving request are refused before any launch
+    n = 126_322_568
+    G = core.Graph(n=n, rowptr=np.zeros(n + 1, np.int32), colids=np.zeros(0, np.int32))
+    L = core.Layout(G, seed=0)
+    with pytest.raises(core.BatchLayoutError) as e:
+        L.run(1, 256, "bh")
+    assert e.value.status == core.BL_EINVAL
+    L.run(0, 256, "bh")   # nothing to do is still fine
+    S = core.Server(1 << 40)
+    try:
+        with pytest.raises(core.BatchLayoutError) as e:
+            S.submit(G, 0, 1, 256, "bh")
+        assert e.value.status == core.BL_EINVAL
+    finally:
+        S.close()
+    L.close()
+    G.close()
