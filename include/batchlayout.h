@@ -155,7 +155,9 @@ bl_status bl_layout_set_positions(bl_layout *L, const float *xy, int64_t start_i
  * iterations give the same positions and energies, bit for bit, as one run of
  * k + m. Synchronises; BL_ETIMEOUT if a bounded device-side wait gave up.
  * BL_BH takes graphs of at most 126,322,567 vertices (its quadtree reserves
- * 17 n + 1 nodes with 32-bit indices); larger ones give BL_EINVAL. */
+ * 17 n + 1 nodes with 32-bit indices); larger ones give BL_EINVAL. A BL_EXACT
+ * call runs at most 2^31 - 1 minibatch steps (iters * ceil(n / batch)); a
+ * longer run is split over several calls, with the same result. */
 bl_status bl_layout_run(bl_layout *L, int32_t iters, int32_t batch, bl_mode mode, float theta);
 
 /* Runs at most max_iters iterations and stops after the first iteration whose

@@ -332,7 +332,17 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
         smp.push_back(work[k]);
         pos_floats += 2 * (size_t)work[k].n;
     }
-    DevBuf pos, en, items, cur;
+    // scratch copies of the sample, freed (after the stream drains) on every return
+    struct Scratch {
+        cudaStream_t st;
+        DevBuf pos, en, items, cur;
+        EventPair ev;
+        ~Scratch() {
+            cudaStreamSynchronize(st);
+            for (DevBuf* b : {&pos, &en, &items, &cur}) b->release();
+        }
+    } sc{st, {}, {}, {}, {}, {}};
+    DevBuf &pos = sc.pos, &en = sc.en, &items = sc.items, &cur = sc.cur;
     BL_TRY(pos.ensure(al, pos_floats * sizeof(float)));
     BL_TRY(en.ensure(al, smp.size() * 10 * sizeof(double)));
     BL_TRY(items.ensure(al, smp.size() * sizeof(BatchItem)));
@@ -349,9 +359,8 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
     }
     BL_CUDA_TRY(cudaMemcpyAsync(items.p, smp.data(), smp.size() * sizeof(BatchItem),
                                 cudaMemcpyHostToDevice, st));
-    cudaEvent_t e0, e1;
-    BL_CUDA_TRY(cudaEventCreate(&e0));
-    BL_CUDA_TRY(cudaEventCreate(&e1));
+    BL_CUDA_TRY(sc.ev.create());
+    const cudaEvent_t e0 = sc.ev.e0, e1 = sc.ev.e1;
     int best = 0;
     float best_ms = 0.f;
     bl_status s = BL_OK;
@@ -372,13 +381,6 @@ bl_status autotune(int ncap, const std::vector<BatchItem>& work, const Allocator
             best_ms = ms;
         }
     }
-    cudaStreamSynchronize(st);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    pos.release();
-    en.release();
-    items.release();
-    cur.release();
     if (s != BL_OK) return s;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;
@@ -521,9 +523,9 @@ bl_status batch_run(bl_layout* const* Ls, int count, int iters, int BS, int chun
         if (fits) small.push_back(BatchJob{Ls[k], iters, BS});
         else big.push_back(Ls[k]);
     }
-    cudaEvent_t e0, e1;
-    BL_CUDA_TRY(cudaEventCreate(&e0));
-    BL_CUDA_TRY(cudaEventCreate(&e1));
+    EventPair ev;
+    BL_CUDA_TRY(ev.create());
+    const cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     BL_CUDA_TRY(cudaEventRecord(e0, st));
     bl_status s = batch_launch(small.data(), (int)small.size(), chunk, st);
     for (size_t q = 0; q < big.size() && s == BL_OK; q++) {
@@ -545,8 +547,6 @@ bl_status batch_run(bl_layout* const* Ls, int count, int iters, int BS, int chun
         if (elapsed_ms) *elapsed_ms = ms;
         for (int k = 0; k < count; k++) Ls[k]->last_ms = ms;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return s;
 }
 

@@ -772,6 +772,9 @@ bl_status exact_launch(const ExactPlan& pl, const ExactTask& task, const ExactPa
                        cudaStream_t st) {
     if (task.n <= 0) return BL_OK;
     if (task.BS > kMaxBatch) return set_error(BL_EINVAL, "exact engine: batch too large");
+    // the kernel counts minibatch steps (iterations x minibatches) in int32
+    if ((int64_t)task.iters * task.B > 0x7fffffffLL)
+        return set_error(BL_EINVAL, "exact engine: more than 2^31 - 1 minibatch steps in one launch");
     switch (pl.T) {
         case 512: return dispatch_rpt<512>(pl, task, prm, st);
         case 448: return launch_grid_t<1, 448>(pl, task, prm, st);

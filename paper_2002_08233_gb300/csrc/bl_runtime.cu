@@ -452,24 +452,23 @@ bl_status bl_layout_run(bl_layout* L, int32_t iters, int32_t batch, bl_mode mode
     if (batch < 1 || batch > kMaxBatch) return set_error(BL_EINVAL, "bl_layout_run: batch must be in [1, 8192]");
     if (mode != BL_EXACT && mode != BL_BH) return set_error(BL_EINVAL, "bl_layout_run: mode must be BL_EXACT or BL_BH");
     if (mode == BL_BH && !(theta >= 0.0f)) return set_error(BL_EINVAL, "bl_layout_run: theta must be >= 0");
+    if (mode == BL_EXACT && (int64_t)iters * div_up(L->g->n, batch) > 0x7fffffffLL)
+        return set_error(BL_EINVAL, "bl_layout_run: more than 2^31 - 1 minibatch steps in one call; split the run");
     if (iters == 0) return BL_OK;
     cudaStream_t st = current_stream();
-    cudaEvent_t e0, e1;
-    BL_CUDA_TRY(cudaEventCreate(&e0));
-    BL_CUDA_TRY(cudaEventCreate(&e1));
-    BL_CUDA_TRY(cudaEventRecord(e0, st));
+    EventPair ev;
+    BL_CUDA_TRY(ev.create());
+    BL_CUDA_TRY(cudaEventRecord(ev.e0, st));
     bl_status s = mode == BL_EXACT ? exact_run(L, iters, batch, false, nullptr, st)
                                    : bh_run(L, iters, batch, theta, st);
     if (s == BL_OK) {
-        BL_CUDA_TRY(cudaEventRecord(e1, st));
-        BL_CUDA_TRY(cudaEventSynchronize(e1));
+        BL_CUDA_TRY(cudaEventRecord(ev.e1, st));
+        BL_CUDA_TRY(cudaEventSynchronize(ev.e1));
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventElapsedTime(&ms, ev.e0, ev.e1);
         L->last_ms = ms;
         s = check_stream_status(L);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (s != BL_OK) return s;
     const double n = (double)L->g->n;
     L->last_iters = iters;

@@ -87,3 +87,18 @@ def test_bh_rejects_graphs_over_its_vertex_limit(core):
         S.close()
     L.close()
     G.close()
+
+
+def test_exact_run_refuses_more_steps_than_int32_counts(core):
+    # 536,871 iterations x 4,000 minibatches of one vertex > 2^31 - 1 steps: refused
+    # before any launch, and the layout is left as it was
+    g = synth.erdos_renyi(4000, 5.0, 3)
+    G = core.Graph(g)
+    L = core.Layout(G, seed=3)
+    with pytest.raises(core.BatchLayoutError) as e:
+        L.run(536_871, 1, "exact")
+    assert e.value.status == core.BL_EINVAL
+    L.run(1, 1, "exact")
+    ref = core.Layout(G, seed=3)
+    ref.run(1, 1, "exact")
+    assert np.array_equal(L.positions(), ref.positions())
