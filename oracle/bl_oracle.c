@@ -34,7 +34,7 @@
  *   R7  BH tree built once per iteration from the snapshot S of the positions
  *       at iteration start (Algorithm S5 builds it before the batch loop);
  *       attraction uses the live positions.
- *   R8  "re-scale c in bounding box" does not move vertices: the box only
+ *   R8  Algorithm S5's bounding-box rescaling does not move vertices: the box only
  *       quantises positions to Morton codes; the root square has side
  *       D = max(xmax-xmin, ymax-ymin) anchored at (xmin, ymin).
  *   R9  Morton codes in FP32, no contraction: s = 65536/D;

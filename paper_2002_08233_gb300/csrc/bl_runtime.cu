@@ -478,8 +478,8 @@ bl_status bl_layout_run(bl_layout* L, int32_t iters, int32_t batch, bl_mode mode
     return BL_OK;
 }
 
-// Runs until the energy settles (Section 4.5 runs "until convergence": the
-// energy difference between successive iterations below 1e-6; read relatively,
+// Runs until the energy settles (Section 4.5 runs layouts to convergence, with
+// successive iterations' energies differing by less than 1e-6; read relatively,
 // |E_t - E_{t-1}| <= tol * max(E_{t-1}, 1), as energies are sums over all
 // vertices). Iterations run in chunks; when the rule holds inside a chunk, the
 // chunk's start positions are restored and only the iterations up to that point

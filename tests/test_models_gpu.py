@@ -40,13 +40,21 @@ def test_snapshot_forces(core, model, a, mode):
 
 
 @pytest.mark.parametrize("model,a", MODELS)
-@pytest.mark.parametrize("engine", ["exact", "bh", "batched"])
+@pytest.mark.parametrize("engine", ["exact", "exact_grid", "bh", "batched"])
 def test_one_iteration(core, model, a, engine):
+    """exact: the default engine at this size (one thread-block cluster);
+    exact_grid: the whole-GPU engine forced."""
     g = synth.grid2d(20, 25)
     xy = synth.uniform_positions(g.n, 7)
     L = core.Layout(core.Graph(g), xy=xy, model=model)
     if engine == "batched":
         core.run_batch([L], 1, 64)
+    elif engine == "exact_grid":
+        os.environ["BL_EXACT_ENGINE"] = "grid"
+        try:
+            L.run(1, 64, "exact")
+        finally:
+            os.environ.pop("BL_EXACT_ENGINE", None)
     else:
         L.run(1, 64, engine, 1.2)
     mode = oracle.BH if engine == "bh" else oracle.EXACT
