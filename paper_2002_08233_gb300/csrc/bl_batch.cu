@@ -88,7 +88,7 @@ __device__ __forceinline__ void phase_a(const float4* __restrict__ s_pos4, int n
         }
         for (int qc = s; qc < np; qc += kStripes * kFold) {
             const int kend = min(kFold, (np - qc + kStripes - 1) / kStripes);
-#pragma unroll 4
+#pragma unroll 16   // a whole fold: 16 column pairs of loads and reciprocals in flight
             for (int k = 0; k < kend; k++) {
                 const float4 p = s_pos4[qc + k * kStripes];
                 const f32x2 X = pk2(p.x, p.y), Y = pk2(p.z, p.w);
