@@ -584,7 +584,8 @@ def main():
             print(json.dumps({"only": args.only, **line}))
         return
     out, g = run_exact(args, rank, world, local)
-    if not args.no_also:
+    # the secondary lines are one-GPU measurements: only a single-process run makes them
+    if not args.no_also and world == 1:
         also = {}
         for name, fn in (("bh_rmat20", run_bh), ("grid32_600it", run_grid),
                          ("batched_4096", run_batched), ("serving", run_serving)):
