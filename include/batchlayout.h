@@ -184,6 +184,7 @@ bl_status bl_positions_device(const bl_layout *L, void **dptr);
 bl_status bl_energy_history(const bl_layout *L, double *out, int64_t cap, int64_t *count);
 
 bl_status bl_stats(const bl_layout *L, bl_stats_t *out);
+/* Frees the layout after the library's stream (bl_set_stream) has drained. */
 void bl_layout_free(bl_layout *L);
 
 /* ---- quality (Section 3.7) --------------------------------------------------- */

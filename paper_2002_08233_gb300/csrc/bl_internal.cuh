@@ -201,6 +201,10 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
 // SplitMix64-seeded positions uniform in [-1, 1), as bl_layout_init draws them.
 void seeded_positions(int32_t n, uint64_t seed, float* xy);
 
+// Frees a layout without synchronising: the caller has drained the stream its
+// work ran on (bl_runtime.cu).
+void layout_destroy(bl_layout* L);
+
 // A layout whose positions are uploaded from xy (2n floats) or drawn from seed,
 // without waiting for the upload (bl_runtime.cu). xy must stay valid until the
 // stream reaches the copy.

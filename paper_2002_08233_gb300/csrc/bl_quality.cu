@@ -394,11 +394,15 @@ __global__ void eu_mean_kernel(const double* part_s, const unsigned long long* p
     }
 }
 
-// Scratch of one bl_quality call, released when it goes out of scope (after the
-// stream has been synchronised).
+// Scratch of one bl_quality call, released when it goes out of scope, on every
+// return path, once the stream has drained (a caller's allocator may hand the
+// memory out again at once).
 struct QScratch {
+    cudaStream_t st;
     DevBuf vis, fa, fb, cnt, bar, pa, pb, pp, src, lkey, lid, jac, inter, queries, eu;
+    explicit QScratch(cudaStream_t s) : st(s) {}
     ~QScratch() {
+        cudaStreamSynchronize(st);
         for (DevBuf* b : {&vis, &fa, &fb, &cnt, &bar, &pa, &pb, &pp, &src, &lkey, &lid, &jac, &inter,
                           &queries, &eu})
             b->release();
@@ -416,7 +420,7 @@ bl_status quality_run(bl_layout* L, int32_t nsources, int32_t nqueries, uint64_t
     const int* colids = L->g->colids.as<int>();
     const float2* pos = L->pos.as<float2>();
     const Allocator& al = L->alloc;
-    QScratch s;
+    QScratch s(st);
     const int sms = device_sm_count();
 
     // ---- stress ----

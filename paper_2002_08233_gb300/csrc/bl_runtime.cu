@@ -210,6 +210,20 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
 }  // namespace bl
 
 namespace bl {
+// Frees a layout's device memory; the caller has drained the stream its work ran on.
+void layout_destroy(bl_layout* L) {
+    if (!L) return;
+    if (L->bh) bh_state_free(L->bh);
+    L->pos.release();
+    L->pos2.release();
+    L->energy.release();
+    L->epart.release();
+    L->status.release();
+    L->scratch.release();
+    L->trace.release();
+    delete L;
+}
+
 bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64_t start_iter,
                         const bl_force_params* params, bool sync, cudaStream_t st, bl_layout** out) {
     if (!out) return set_error(BL_EINVAL, "bl_layout_init: out is NULL");
@@ -244,7 +258,8 @@ bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64
         if (e != cudaSuccess) s = cuda_error(e, "bl_layout_init: upload");
     }
     if (s != BL_OK) {
-        bl_layout_free(L);
+        cudaStreamSynchronize(st);
+        layout_destroy(L);
         return s;
     }
     *out = L;
@@ -601,15 +616,8 @@ bl_status bl_stats(const bl_layout* L, bl_stats_t* out) {
 
 void bl_layout_free(bl_layout* L) {
     if (!L) return;
-    if (L->bh) bh_state_free(L->bh);
-    L->pos.release();
-    L->pos2.release();
-    L->energy.release();
-    L->epart.release();
-    L->status.release();
-    L->scratch.release();
-    L->trace.release();
-    delete L;
+    cudaStreamSynchronize(current_stream());   // nothing of this layout may still be running
+    layout_destroy(L);
 }
 
 bl_status bl_quality(const bl_layout* L, int32_t nsources, int32_t nqueries, uint64_t seed,

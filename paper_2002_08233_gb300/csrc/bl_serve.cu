@@ -123,7 +123,10 @@ void retire(bl_server* S, Job* j, bl_status err) {
         if (e != cudaSuccess) err = cuda_error(e, "server: result copy");
     }
     if (err != BL_OK && j->msg.empty()) j->msg = bl_last_error();
-    if (j->L) bl_layout_free(j->L);
+    if (j->L) {
+        cudaStreamSynchronize(S->st);   // the job's work ran on the server's stream
+        layout_destroy(j->L);
+    }
     j->L = nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
     j->t_done = Clock::now();
@@ -222,11 +225,11 @@ void worker_main(bl_server* S) {
         std::lock_guard<std::mutex> lk(S->mu);
         left = S->active;
     }
+    cudaStreamSynchronize(S->st);
     for (Job* j : left) {
-        if (j->L) bl_layout_free(j->L);
+        if (j->L) layout_destroy(j->L);
         j->L = nullptr;
     }
-    cudaStreamSynchronize(S->st);
 }
 
 }  // namespace
