@@ -59,3 +59,8 @@ def test_reference_arm_prints_one_line_from_rank_zero():
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the same workload description, metric and direction as the CUDA arm's line
+    assert "Barabasi-Albert n=65,536" in d["config"]["workload"]
+    assert d["config"]["iterations_per_step"] == 10 and d["config"]["batch"] == 256
+    assert d["unit"] == "pair-interactions/s" and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["cores"] >= 1
