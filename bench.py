@@ -557,9 +557,15 @@ def run_serving(args, local):
 
     wall_sat, st_sat = serve([0.0] * len(reqs))
     thr = len(reqs) / wall_sat
-    lam = 0.8 * thr
-    arr = np.array([r.arrival_s for r in reqs]) / lam   # the seeded unit-rate gaps, rescaled
-    wall_p, st_p = serve(list(arr))
+    unit_gaps = np.array([r.arrival_s for r in reqs])   # the seeded unit-rate arrivals
+    sweep = {}
+    for f in (0.5, 0.8, 1.0, 1.2):   # offered load as a fraction of the saturated rate
+        lam_f = f * thr
+        wall_f, st_f = serve(list(unit_gaps / lam_f))
+        sweep[f"{f}x"] = {"rate_per_s": lam_f, "layouts_per_s": len(reqs) / wall_f,
+                          "p50_s": st_f["p50_s"], "p99_s": st_f["p99_s"]}
+        if f == 0.8:
+            lam, wall_p, st_p = lam_f, wall_f, st_f
     return {
         "workload": f"serving: first {count} requests of the seeded Poisson stream (seed 5), n "
                     "log-uniform [1e3, 2e6], half R-MAT edge factor 8, half triangulated meshes, "
@@ -570,6 +576,7 @@ def run_serving(args, local):
         "poisson_0.8x": {"rate_per_s": lam, "layouts_per_s": len(reqs) / wall_p, "seconds": wall_p,
                          "p50_s": st_p["p50_s"], "p99_s": st_p["p99_s"],
                          "peak_bytes": st_p["peak_bytes"]},
+        "rate_sweep": sweep,
         "vertices": int(sum(g.n for g in Gs)),
     }
 
