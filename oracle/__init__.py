@@ -56,6 +56,7 @@ def _load():
             lib.orc_morton.argtypes = [i32, P, P, P, P]
             lib.orc_bh_tree.argtypes = [i32, P, P, P, P, i32, P, P, P, P, P, P, P]
             lib.orc_bh_interactions.argtypes = [i32, P, P, f64, P, P]
+            lib.orc_bh_query_counts.argtypes = [i32, P, P, f64, P, P]
             lib.orc_stress.argtypes = [i32, P, P, P, i32, P, P]
             lib.orc_edge_uniformity.argtypes = [i32, P, P, P, P]
             lib.orc_neighborhood_preservation.argtypes = [i32, P, P, P, i32, P, P]
@@ -166,6 +167,21 @@ def bh_interactions(xy, theta=THETA_DEFAULT):
     _check(lib.orc_bh_interactions(a.shape[0], _ptr(xf), _ptr(yf), theta, ctypes.byref(far),
                                    ctypes.byref(near)), "bh_interactions")
     return far.value, near.value
+
+
+def bh_query_counts(xy, theta=THETA_DEFAULT):
+    """Per vertex: (accepted far-field nodes, leaf vertices met, its own included)
+    on its walk of the quadtree (Section 3.5's MAC, Algorithm S4)."""
+    lib = _load()
+    a = np.asarray(xy, dtype=np.float32).reshape(-1, 2)
+    n = a.shape[0]
+    xf = np.ascontiguousarray(a[:, 0])
+    yf = np.ascontiguousarray(a[:, 1])
+    far = np.zeros(max(n, 1), dtype=np.int32)
+    near = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib.orc_bh_query_counts(n, _ptr(xf), _ptr(yf), theta, _ptr(far), _ptr(near)),
+           "bh_query_counts")
+    return far[:n].copy(), near[:n].copy()
 
 
 def stress(g, xy, sources=None):

@@ -550,6 +550,24 @@ int orc_bh_interactions(int n, const float *xf, const float *yf, double theta,
     return ORC_OK;
 }
 
+/* The same MAC decisions query by query: far_out[i] = far-field nodes accepted on
+ * vertex i's walk, near_out[i] = leaf vertices it met (its own included). */
+int orc_bh_query_counts(int n, const float *xf, const float *yf, double theta,
+                        int *far_out, int *near_out)
+{
+    otree t;
+    int rc = tree_build(&t, n, xf, yf);
+    if (rc != ORC_OK) return rc;
+    for (int i = 0; i < n; i++) {
+        long long f = 0, m = 0;
+        if (t.nnodes > 0) walk_counts(&t, 0, xf[i], yf[i], (float)theta, &f, &m);
+        far_out[i] = (int)f;
+        near_out[i] = (int)m;
+    }
+    tree_free(&t);
+    return ORC_OK;
+}
+
 /* -------------------------------------------------------------------------- */
 /* Quality metrics, Section 3.7                                                */
 /* -------------------------------------------------------------------------- */

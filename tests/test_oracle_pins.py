@@ -407,6 +407,152 @@ def test_bh_error_shrinks_with_theta():
     assert errs[1] < 0.05
 
 
+def _dense_bh_theta0_run(A, xy, iters, BS, K, R, rn, start_iter=0):
+    """Algorithm S5 by brute force over the dense adjacency matrix at theta = 0,
+    where no node passes the MAC and the tree repulsion is the plain sum over every
+    other vertex. Per iteration the repulsion is taken once, at the snapshot S of
+    the positions at iteration start as the quadtree stores them (FP32, reading
+    R7), and without the neighbours unless rn; the attraction of each minibatch is
+    taken at the live positions (earlier minibatches already moved)."""
+    xy = xy.copy()
+    n = xy.shape[0]
+    step = 1.0
+    for _ in range(start_iter):
+        step *= 0.999
+    eye = np.eye(n, dtype=bool)
+    wrep = ~eye if rn else (~eye & (A == 0))
+    energies = []
+    for _ in range(iters):
+        S = xy.astype(np.float32).astype(np.float64)
+        dS = S[None, :, :] - S[:, None, :]
+        d2S = (dS ** 2).sum(-1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rep = np.where(wrep & (d2S > 0), -R * K * K / d2S, 0.0)
+        Frep = (rep[:, :, None] * dS).sum(axis=1)
+        E = 0.0
+        for lo in range(0, n, BS):
+            hi = min(n, lo + BS)
+            diff = xy[None, :, :] - xy[lo:hi, None, :]
+            d = np.sqrt((diff ** 2).sum(-1))
+            att = A[lo:hi] * np.where(d > 0, d / K, 0.0)       # (d^2/K)/d
+            F = (att[:, :, None] * diff).sum(axis=1) + Frep[lo:hi]
+            for k, i in enumerate(range(lo, hi)):
+                nf = math.hypot(F[k, 0], F[k, 1])
+                if nf > 0:
+                    xy[i] += step * F[k] / nf
+                E += nf * nf
+        energies.append(E)
+        step *= 0.999
+    return xy, np.array(energies)
+
+
+@pytest.mark.parametrize("BS", [1, 3, 12])
+@pytest.mark.parametrize("rn", [False, True])
+def test_bh_run_matches_dense_snapshot_loop(BS, rn):
+    """The oracle's Barnes-Hut iteration (Algorithm S5) at theta = 0 against the
+    dense brute force above: the tree is built once per iteration from the
+    snapshot, the attraction follows the live positions. Rebuilding the tree per
+    minibatch, or taking the attraction at the snapshot, fails this."""
+    n = 13
+    rng = np.random.default_rng(200 + BS + 7 * rn)
+    A = np.triu((rng.random((n, n)) < 0.3).astype(np.int64), 1)
+    A = A + A.T
+    iu, ju = np.nonzero(np.triu(A, 1))
+    g = synth.csr_from_edges(n, iu, ju)
+    xy = rng.uniform(-1, 1, size=(n, 2))
+    x1, e1 = oracle.run(g, xy, iters=3, batch=BS, mode=oracle.BH, theta=0.0, repulse_neighbors=rn,
+                        start_iter=4)
+    x2, e2 = _dense_bh_theta0_run(A, xy, 3, BS, 1.0, 1.0, rn, start_iter=4)
+    assert np.allclose(x1, x2, rtol=1e-10, atol=1e-10)
+    assert np.allclose(e1, e2, rtol=1e-10)
+
+
+def _pair_bh_gauss_seidel(x0, x1, iters, K, start_iter):
+    """Two vertices joined by an edge on the x axis, minibatch 1, repulsion
+    between them (repulse_neighbors): vertex 0 moves, then vertex 1. The
+    attraction follows the live positions, the repulsion the iteration's snapshot
+    (FP32, as the tree stores it), and each vertex moves by Step towards the sign
+    of its net force."""
+    step = 1.0
+    for _ in range(start_iter):
+        step *= 0.999
+    out = []
+    for _ in range(iters):
+        s0, s1 = float(np.float32(x0)), float(np.float32(x1))
+        dS = abs(s1 - s0)
+        f0 = math.copysign((x1 - x0) ** 2 / K, x1 - x0) + math.copysign(K * K / dS, s0 - s1)
+        x0 += math.copysign(step, f0)
+        f1 = math.copysign((x0 - x1) ** 2 / K, x0 - x1) + math.copysign(K * K / dS, s1 - s0)
+        x1 += math.copysign(step, f1)
+        out.append((x0, x1, f0 * f0 + f1 * f1))
+        step *= 0.999
+    return out
+
+
+def test_bh_two_vertex_trajectory_closed_form():
+    """At d = 1.4 and Step ~ 0.5 vertex 0 is pulled to d = 0.9; vertex 1 then
+    feels the live attraction 0.81 against the snapshot repulsion 1/1.4 and is
+    pulled too, where the exact mode (repulsion 1/0.9) would push it away."""
+    g = synth.from_edge_list(2, [(0, 1)])
+    x0, x1, start = 0.0, 1.4, 693
+    expect = _pair_bh_gauss_seidel(x0, x1, 6, 1.0, start)
+    x = np.array([[x0, 0.0], [x1, 0.0]])
+    for t in range(6):
+        x, e = oracle.run(g, x, iters=1, batch=1, mode=oracle.BH, theta=1.2, repulse_neighbors=True,
+                          start_iter=start + t)
+        assert x[0, 0] == pytest.approx(expect[t][0], abs=1e-12), t
+        assert x[1, 0] == pytest.approx(expect[t][1], abs=1e-12), t
+        assert e[0] == pytest.approx(expect[t][2], rel=1e-12), t
+        assert np.all(x[:, 1] == 0.0)
+    assert expect[0][1] < 1.0        # pulled in the first iteration
+    xe, _ = oracle.run(g, np.array([[x0, 0.0], [x1, 0.0]]), iters=1, batch=1, repulse_neighbors=True,
+                       start_iter=start)
+    assert xe[1, 0] > 1.8            # the exact mode pushes vertex 1 away instead
+
+
+def _fig4_grid():
+    """16 vertices at the centres of a 4 x 4 grid of cells in [0,1]^2 (Fig. 4):
+    root side D = 0.75, four quadrant nodes, sixteen one-vertex leaves."""
+    c = (np.arange(4) + 0.5) / 4.0
+    X, Y = np.meshgrid(c, c)
+    return np.stack([X.ravel(), Y.ravel()], axis=1).astype(np.float32)
+
+
+def test_bh_mac_counts_fig4_grid_by_hand():
+    """MAC decisions counted by hand on the Fig. 4 grid. The root (D^2 = 0.5625)
+    never passes for theta <= 1.2 (every vertex is within d^2 = 0.28125 of the
+    centre). A quadrant node (D^2 = 0.140625) passes at theta = 1.2 when
+    d^2 > 0.0977 (every other quadrant: 3 far nodes, 4 leaves per vertex) and at
+    theta = 0.6 when d^2 > 0.390625: a corner vertex accepts the 3 other quadrants
+    (4 leaves), a vertex with one coordinate on the rim accepts 2 (8 leaves), an
+    inner vertex none (16 leaves)."""
+    xy = _fig4_grid()
+    assert oracle.bh_interactions(xy, 1.2) == (48, 64)
+    assert oracle.bh_interactions(xy, 0.6) == (4 * 7, 4 * 36)
+    assert oracle.bh_interactions(xy, 0.0) == (0, 256)       # every leaf, no far node
+    assert oracle.bh_interactions(xy, 1e18) == (16, 0)       # the root, for all 16
+    far, near = oracle.bh_query_counts(xy, 0.6)
+    rim = ((xy == np.float32(0.125)) | (xy == np.float32(0.875))).sum(axis=1)
+    expect_far = np.choose(rim, [0, 2, 3])
+    expect_near = np.choose(rim, [16, 8, 4])
+    assert np.array_equal(far, expect_far) and np.array_equal(near, expect_near)
+    far, near = oracle.bh_query_counts(xy, 1.2)
+    assert np.all(far == 3) and np.all(near == 4)
+
+
+def test_bh_mac_counts_limits_random():
+    """theta = 0: no node is accepted and every query meets all n vertices at the
+    leaves (distinct codes); a huge theta accepts the root once per vertex that
+    is not at the centroid."""
+    xy = synth.uniform_positions(500, 17)
+    far, near = oracle.bh_query_counts(xy, 0.0)
+    assert np.all(far == 0) and np.all(near == 500)
+    far, near = oracle.bh_query_counts(xy, 1e18)
+    assert np.all(far == 1) and np.all(near == 0)
+    assert oracle.bh_interactions(xy, 0.7) == (int(oracle.bh_query_counts(xy, 0.7)[0].sum()),
+                                              int(oracle.bh_query_counts(xy, 0.7)[1].sum()))
+
+
 # ---------------------------------------------------------------------------
 # quality metrics (Section 3.7)
 # ---------------------------------------------------------------------------
@@ -429,6 +575,33 @@ def test_stress_unit_square_closed_form():
     assert st == pytest.approx((12 - 8 * r2) / 5, rel=1e-12)
     st2, _, _ = oracle.stress(g, xy * 7.5)
     assert st2 == pytest.approx(st, rel=1e-12)
+
+
+def test_stress_every_source_sampled_equals_all_pairs():
+    """With every vertex as a sampled source each unordered pair is met twice:
+    the ordered sums double and the n / (2 n) rescale restores the all-pairs
+    stress; the optimal scale is unchanged and the pair count doubles."""
+    g = synth.erdos_renyi(40, 4.0, 7)
+    xy = synth.uniform_positions(40, 7)
+    st, s, p = oracle.stress(g, xy)
+    st2, s2, p2 = oracle.stress(g, xy, sources=np.arange(40))
+    assert p2 == 2 * p
+    assert st2 == pytest.approx(st, rel=1e-12)
+    assert s2 == pytest.approx(s, rel=1e-12)
+
+
+def test_stress_sampled_sources_by_hand():
+    """Path 0-1-2-3 drawn at x = 0, 1, 3, 6 plus an isolated vertex 4.
+    Source 0: hop distances 1, 2, 3, layout distances 1, 3, 6, so x/d = 1, 1.5, 2:
+    a = 9/2, b = 29/4, stress = 3 - a^2/b = 6/29, scaled by n/(2 ns) = 5/2.
+    Sources {0, 3}: source 3 adds x/d = 2, 2.5, 3: a = 12, b = 53/2,
+    stress = 6 - 288/53 = 30/53, scaled by 5/4. Vertex 4 is unreachable."""
+    g = synth.from_edge_list(5, [(0, 1), (1, 2), (2, 3)])
+    xy = np.array([[0, 0], [1, 0], [3, 0], [6, 0], [100, 0]], dtype=np.float64)
+    st, s, p = oracle.stress(g, xy, sources=[0])
+    assert (st, s, p) == (pytest.approx(2.5 * 6 / 29, rel=1e-13), pytest.approx(18 / 29, rel=1e-13), 3)
+    st, s, p = oracle.stress(g, xy, sources=[0, 3])
+    assert (st, s, p) == (pytest.approx(1.25 * 30 / 53, rel=1e-13), pytest.approx(24 / 53, rel=1e-13), 6)
 
 
 def test_neighborhood_preservation_closed_forms():
