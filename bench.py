@@ -352,7 +352,27 @@ def run_reference(args, rank, world):
 # secondary: Barnes-Hut, R-MAT scale 20
 # ---------------------------------------------------------------------------
 
+def bh_bytes(n, nnz, nnz_early, nodes):
+    """Algorithmic bytes of one Barnes-Hut iteration (what each phase must move at
+    least once), by phase. The whole iteration's figure follows the per-unit
+    counts of the path: bounding box 8n, Morton codes 12n, four sort passes of 16n
+    (keys and values read and written), the tree ~32 B per node plus 8n of codes,
+    the CSR work 12 B per edge (column id + neighbour position) plus 16 B per
+    vertex; the walk's node records are counted apart (they are L2 reads)."""
+    phases = {
+        "bbox_morton": 24 * n,                     # bbox read 8n, Morton read 8n, keys+values 8n
+        "radix_sort": 4 * 16 * n,
+        "tree": 28 * n + 48 * nodes,               # sorted copy 20n, codes 8n, node fields 48 B
+        "edge_pass": 12 * nnz + 32 * n,            # every edge once; rowptr, split, S, two outputs
+        "sweep": 12 * nnz_early + 48 * n,          # earlier-minibatch edges again; per-row state
+        "energy": 8 * n,
+    }
+    total = 8 * n + 12 * n + 64 * n + (32 * nodes + 8 * n) + 12 * nnz + 16 * n
+    return phases, total
+
+
 def run_bh(args, local, steps=5, warmup=2):
+    import numpy as np
     import torch
 
     from paper_2002_08233_gb300 import core, synth
@@ -375,18 +395,86 @@ def run_bh(args, local, steps=5, warmup=2):
     ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     st = L.stats()
     total = sum(ms)
+    ms_it = total / steps
+    # phases of 3 more iterations (events between phases; not part of the timed steps)
+    L.set_phase_timing(True)
+    L.run(3, BATCH, "bh", 1.2)
+    ph = L.phase_times()
+    L.set_phase_timing(False)
+    rows = np.repeat(np.arange(n), np.diff(g.rowptr))
+    nnz_early = int(np.count_nonzero(g.colids < (rows // BATCH) * BATCH))
+    pbytes, tbytes = bh_bytes(n, g.nnz, nnz_early, ph["nodes"])
+    pk, src = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0)) * 1e9
+    it = max(ph["iterations"], 1)
+    phases = {}
+    for name in L.PHASES:
+        t_ms = ph[name] / it
+        d = {"ms_per_iteration": t_ms, "share": t_ms / (ph["iteration"] / it)}
+        if name in pbytes and t_ms > 0:
+            d["bytes"] = pbytes[name]
+            d["achieved_gbs"] = pbytes[name] / (t_ms / 1e3) / 1e9
+            d["frac_hbm"] = pbytes[name] / (t_ms / 1e3) / hbm
+        phases[name] = d
+    phases["walk"]["node_record_bytes_l2"] = 24 * ph["walk_warp_visits"]
+    achieved = tbytes / (ms_it / 1e3)
+    # end to end through the public API: positions up, one iteration, positions down
+    x0 = synth.uniform_positions(n, 0)
+    host_in = torch.from_numpy(x0.copy()).pin_memory()
+    host_out = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    hin, hout = host_in.numpy(), host_out.numpy()
+    L2 = core.Layout(G, seed=0)
+    L2.run(1, BATCH, "bh", 1.2)
+    torch.cuda.synchronize()
+    e2e_steps = 5
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        L2.set_positions(hin, start_iter=k)
+        L2.run(1, BATCH, "bh", 1.2)
+        L2.positions(out=hout)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
     return {
         "workload": f"Barnes-Hut BatchLayout, R-MAT scale {args.bh_scale} (n={n:,}, edge factor "
                     "16, a=.57 b=c=.19), minibatch 256, theta 1.2, one iteration per step",
         "metric": "vertex-updates/s", "value": n * steps / (total / 1e3),
-        "ms_per_iteration": total / steps, "steps": steps, "warmup": warmup,
-        "n": n, "nnz": g.nnz,
+        "ms_per_iteration": ms_it, "steps": steps, "warmup": warmup,
+        "n": n, "nnz": g.nnz, "nnz_earlier_minibatch": nnz_early, "tree_nodes": ph["nodes"],
         "tree_walk_far_nodes": st["bh_far_nodes"], "tree_walk_leaf_vertices": st["bh_near_pairs"],
         # far-field nodes accepted plus leaf vertices met (each query's own excluded),
         # per second of whole iteration
-        "interactions_per_s": (st["bh_far_nodes"] + st["bh_near_pairs"] - n) / (total / steps / 1e3),
-        "l2": "working set > L2 (positions, sorted copies and a ~2n-node tree)",
+        "interactions_per_s": (st["bh_far_nodes"] + st["bh_near_pairs"] - n) / (ms_it / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "algorithmic_bytes_per_iteration": tbytes,
+                     "bytes_note": "172 n + 12 nnz (+ 32 B per tree node over 2n): bbox, Morton, 4 sort "
+                                   "passes, tree, CSR; walk node records not counted (L2 reads)",
+                     "peak_source": f"{src} hbm_gbs"},
+        "phases": phases,
+        "e2e": {"value": n * e2e_steps / e2e_s, "unit": "vertex-updates/s",
+                "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4),
+                "steps": e2e_steps},
+        "l2": "working set > L2 (positions, sorted copies and a ~1.3n-node tree)",
     }
+
+
+def cpu_baseline_bh(g, seconds_target=10.0):
+    """The FP64 oracle's Barnes-Hut iteration (Algorithm S5) on all host cores,
+    from the seeded start: one probe iteration, then as many as fit ~10 s."""
+    import oracle
+    from paper_2002_08233_gb300 import synth
+    cores = os.cpu_count() or 1
+    x0 = synth.uniform_positions(g.n, 0)
+    t0 = time.perf_counter()
+    x1, _ = oracle.run(g, x0, iters=1, batch=BATCH, mode=oracle.BH, theta=1.2, nthreads=cores)
+    probe = time.perf_counter() - t0
+    iters = int(max(1, min(20, round(seconds_target / max(probe, 1e-3)))))
+    t0 = time.perf_counter()
+    oracle.run(g, x1, iters=iters, batch=BATCH, mode=oracle.BH, theta=1.2, start_iter=1, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": g.n * iters / dt, "unit": "vertex-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"iterations 1..{iters} of the Barnes-Hut layout, FP64, OpenMP over each minibatch",
+            "seconds": dt}
 
 
 # ---------------------------------------------------------------------------
@@ -613,6 +701,14 @@ def main():
                 out["cpu_baseline"] = cpu_baseline_exact(g)
             except Exception as e:   # the baseline is context; never fail the bench on it
                 out["cpu_baseline"] = {"error": str(e)}
+            bh = out.get("also", {}).get("bh_rmat20")
+            if bh is not None and "error" not in bh:
+                try:
+                    from paper_2002_08233_gb300 import synth
+                    bh["cpu_baseline"] = cpu_baseline_bh(synth.rmat_scale20() if args.bh_scale == 20 else
+                                                         synth.rmat(args.bh_scale, 16, seed=3))
+                except Exception as e:
+                    bh["cpu_baseline"] = {"error": str(e)}
         print(json.dumps(out))
 
 

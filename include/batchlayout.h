@@ -71,8 +71,13 @@ typedef struct bl_server bl_server;
 /* Force model parameters (Section 2.2). K: optimal spring length; R: relative
  * strength of repulsion. repulse_neighbors = 0 (default) repels non-adjacent
  * pairs only, as the combined force f(i,c) states; 1 repels every pair j != i,
- * as Algorithm S5's tree repulsion does literally. kahan: 1 = compensated FP32
- * repulsion sums, 0 = plain, -1 = automatic (on for n >= 2^20). energy_model
+ * as Algorithm S5's tree repulsion does literally. kahan: 1 = compensated (Kahan)
+ * FP32 repulsion sums, 0 = plain FP32 sums, -1 (default) = compensated from
+ * 1,000,000 vertices on; other values give BL_EINVAL. What is compensated: the
+ * whole-GPU exact engine adds each row's column-tile partial sums (256 columns
+ * at minibatch 256) with compensation; the one-cluster engine compensates every
+ * term of each lane's strided sum; the batched kernel each stripe's folds of 32
+ * columns; Barnes-Hut every node and leaf term of the walk. energy_model
  * picks the (a,r)-energy model, attraction |c_i - c_j|^a / K with repulsion
  * R K^2 / |c_i - c_j| (r = -1): BL_MODEL_FR (a = 2, Fruchterman-Reingold, the
  * default and the paper's reported model), BL_MODEL_FA (a = 1, ForceAtlas),
@@ -286,8 +291,11 @@ void bl_server_free(bl_server *S);
  * call cudaMalloc (an engine that hands out all device memory from its own pool,
  * a serving loop that must not stall on an allocation's implicit
  * synchronisation, a process under a hard device-memory quota).
- * Runs `iters` exact-mode iterations (same engine as bl_layout_run with
- * BL_EXACT) on buffers the caller owns, all device pointers: d_rowptr[n+1] and
+ * Runs `iters` exact-mode iterations on the whole-GPU engine (the one
+ * bl_layout_run uses for BL_EXACT above 3,072 vertices; for smaller graphs
+ * bl_layout_run picks the one-cluster engine, whose results agree within the
+ * exact-mode tolerance, not bit for bit) on buffers the caller owns, all device
+ * pointers: d_rowptr[n+1] and
  * d_colids[nnz] a CSR that already satisfies bl_graph_load_csr's rules (not
  * checked here), d_xy[2n] positions (in/out), d_energy[iters] per-iteration
  * energy (out, may be NULL). params may be NULL (defaults as bl_layout_init);
@@ -297,10 +305,12 @@ void bl_server_free(bl_server *S);
  * Allocates nothing: the engine's working memory lives in one file-scope
  * device array of about 2 MiB that every GPU loading the library holds until
  * exit. Limits: n <= 131072 and iters x (CTAs, at most one per SM) <= 131072;
- * larger requests return BL_EINVAL. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture. All calls share the array: calls that overlap on the
- * GPU (other host threads, other streams) race and must be serialised by the
+ * larger requests return BL_EINVAL, as do K or R not positive and finite. The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), and so does the first call after that device's
+ * context has changed (cudaDeviceReset); make that first call before any
+ * stream capture. All calls share the array: calls that overlap on the GPU
+ * (other host threads, other streams) race and must be serialised by the
  * caller. */
 bl_status bl_layout_run_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colids,
                                 float *d_xy, int32_t iters, int32_t batch,
@@ -333,6 +343,13 @@ bl_status bl_debug_bh_tree(bl_layout *L, uint32_t *codes, int32_t *perm, int32_t
                            int32_t *count, int32_t *level, int32_t *skip, float *sumx,
                            float *sumy, int64_t cap, int64_t *nnodes, float *box);
 
+/* The acceptance decisions of the Barnes-Hut walk (Section 3.5's MAC,
+ * Algorithm S4) query by query, on the tree of the current positions: far[i] =
+ * far-field nodes accepted on vertex i's walk, near[i] = leaf vertices it met
+ * (its own included). Arrays of cap >= n int32, indexed by vertex id.
+ * Synchronises. */
+bl_status bl_debug_bh_counts(bl_layout *L, float theta, int32_t *far, int32_t *near, int64_t cap);
+
 /* ---- profiling hooks ---------------------------------------------------------- */
 
 /* Records device phase timestamps (global timer, ns) for the first max_steps
@@ -345,6 +362,18 @@ bl_status bl_debug_bh_tree(bl_layout *L, uint32_t *codes, int32_t *perm, int32_t
  * iteration's sweep is traced instead: the start time of each of its dependency
  * levels, then its end. */
 bl_status bl_set_trace(bl_layout *L, int32_t max_steps);
+
+/* Phase timing of Barnes-Hut runs (profiling; the paper has no counterpart).
+ * With on != 0, every later BL_BH bl_layout_run of L records CUDA events between
+ * its phases (a little host work per iteration). bl_get_phase_times then gives,
+ * for the last such run, out[0..8] = device milliseconds summed over its
+ * iterations of {bounding box + Morton codes, radix sort, tree + node sums,
+ * theta-walk, wait for the edge pass, minibatch sweep (first level + dataflow),
+ * energy, edge pass (side stream, overlapping the tree and walk), whole
+ * iteration}, out[9] = nodes of the last tree, out[10] = node records read by the
+ * warps of the last walk, out[11] = iterations of that run (cap >= 12). */
+bl_status bl_set_phase_timing(bl_layout *L, int32_t on);
+bl_status bl_get_phase_times(const bl_layout *L, double *out, int64_t cap);
 
 /* Copies the trace of the last traced run: [CTAs][max_steps][12] uint64
  * (exact mode) or [levels + 1] uint64 (BH mode).

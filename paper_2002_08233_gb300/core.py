@@ -85,7 +85,10 @@ def _declare(lib):
         "bl_server_stats": [P, P, i64],
         "bl_debug_forces": [P, ctypes.c_int, f32, i32, i32, P],
         "bl_debug_bh_tree": [P, P, P, P, P, P, P, P, P, i64, P, P],
+        "bl_debug_bh_counts": [P, f32, P, P, i64],
         "bl_set_trace": [P, i32],
+        "bl_set_phase_timing": [P, i32],
+        "bl_get_phase_times": [P, P, i64],
         "bl_get_trace": [P, P, i64, P],
         "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
         "bl_layout_run_batch": [P, i32, i32, i32],
@@ -306,6 +309,29 @@ class Layout:
         out.update(codes=codes, perm=perm, sumx=sx[:m], sumy=sy[:m], nnodes=m,
                    box=tuple(float(b) for b in box))
         return out
+
+    def debug_bh_counts(self, theta: float = THETA_DEFAULT):
+        """Per vertex: (far-field nodes accepted, leaf vertices met) on its walk."""
+        n = self.graph.n
+        far = np.zeros(n, dtype=np.int32)
+        near = np.zeros(n, dtype=np.int32)
+        _check(_lib.bl_debug_bh_counts(self._h, float(theta), _ptr(far), _ptr(near), n))
+        return far, near
+
+    PHASES = ("bbox_morton", "radix_sort", "tree", "walk", "edge_pass_wait", "sweep", "energy",
+              "edge_pass", "iteration")
+
+    def set_phase_timing(self, on: bool = True):
+        _check(_lib.bl_set_phase_timing(self._h, int(bool(on))))
+
+    def phase_times(self) -> dict:
+        """Barnes-Hut phase times of the last timed run (ms summed over its
+        iterations), the last tree's nodes and the walk's node-record reads."""
+        out = np.zeros(12, dtype=np.float64)
+        _check(_lib.bl_get_phase_times(self._h, _ptr(out), out.size))
+        d = {k: float(out[q]) for q, k in enumerate(self.PHASES)}
+        d.update(nodes=int(out[9]), walk_warp_visits=int(out[10]), iterations=int(out[11]))
+        return d
 
     def set_trace(self, max_steps: int):
         _check(_lib.bl_set_trace(self._h, int(max_steps)))

@@ -42,6 +42,7 @@ struct BatchItem {
     int n, BS, iters, rn;
     float invK, negRK2;
     int am;               // attraction exponent a of the (a,-1) model
+    int kahan;            // 1: the folds of each stripe sum compensated
 };
 
 struct BatchArgs {
@@ -66,7 +67,7 @@ __device__ __forceinline__ float2 spos(const float* sp, int i) {
 // Phase A: stripe sums of rows [p0, pend) into part[stripe][row - p0].
 template <int T, int RPT>
 __device__ __forceinline__ void phase_a(const float4* __restrict__ s_pos4, int np, int p0, int pend,
-                                        float2* __restrict__ part) {
+                                        bool kahan, float2* __restrict__ part) {
     constexpr int W = T / 32;
     constexpr int NG = 2 / RPT;   // row groups of 32*RPT rows per pass
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -76,7 +77,7 @@ __device__ __forceinline__ void phase_a(const float4* __restrict__ s_pos4, int n
         const int s = item % kStripes;
         const int gr = item / kStripes;
         f32x2 XI[RPT], YI[RPT], AX[RPT], AY[RPT];
-        float SX[RPT], SY[RPT];
+        float SX[RPT], SY[RPT], CX[RPT], CY[RPT];
 #pragma unroll
         for (int m = 0; m < RPT; m++) {
             const int i = p0 + gr * 32 * RPT + m * 32 + lane;
@@ -84,7 +85,7 @@ __device__ __forceinline__ void phase_a(const float4* __restrict__ s_pos4, int n
             XI[m] = pk2(me.x, me.x);
             YI[m] = pk2(me.y, me.y);
             AX[m] = AY[m] = pk2(0.f, 0.f);
-            SX[m] = SY[m] = 0.f;
+            SX[m] = SY[m] = CX[m] = CY[m] = 0.f;
         }
         for (int qc = s; qc < np; qc += kStripes * kFold) {
             const int kend = min(kFold, (np - qc + kStripes - 1) / kStripes);
@@ -111,15 +112,20 @@ __device__ __forceinline__ void phase_a(const float4* __restrict__ s_pos4, int n
                 float a0, a1, b0, b1;
                 upk2(AX[m], a0, a1);
                 upk2(AY[m], b0, b1);
-                SX[m] += a0 + a1;
-                SY[m] += b0 + b1;
+                if (kahan) {   // compensated over the stripe's folds (uniform branch)
+                    kahan_add(SX[m], CX[m], a0 + a1);
+                    kahan_add(SY[m], CY[m], b0 + b1);
+                } else {
+                    SX[m] += a0 + a1;
+                    SY[m] += b0 + b1;
+                }
                 AX[m] = AY[m] = pk2(0.f, 0.f);
             }
         }
 #pragma unroll
         for (int m = 0; m < RPT; m++) {
             const int r = gr * 32 * RPT + m * 32 + lane;
-            part[s * kRows + r] = make_float2(SX[m], SY[m]);
+            part[s * kRows + r] = make_float2(SX[m] - CX[m], SY[m] - CY[m]);
         }
     }
 }
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(T, (768 / T > 0 ? 768 / T : 1)) batch_kernel(B
                     if (p0 >= r1) break;
                     const int pend = min(p0 + kRows, r1);
                     float2* part = s_part + (pass & 1) * kStripes * kRows;
-                    phase_a<T, RPT>(s_pos4, np, p0, pend, part);
+                    phase_a<T, RPT>(s_pos4, np, p0, pend, g.kahan != 0, part);
                     __syncthreads();
                     // Phase B: virtual thread v -> row v/4, sub-thread v%4
 #pragma unroll
@@ -440,6 +446,7 @@ bl_status batch_launch(const BatchJob* jobs, int count, int chunk, cudaStream_t 
             it.invK = 1.0f / L->prm.K;
             it.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
             it.am = model_exponent(L->prm.energy_model);
+            it.kahan = kahan_on(L->prm.kahan, L->g->n) ? 1 : 0;
             items.push_back(it);
         }
     }

@@ -65,7 +65,7 @@ struct BHState {
     DevBuf lvl;                         // int[64]: per-level counts, offsets, fill
     DevBuf lvl_nodes;                   // nodes bucketed by level
     DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
-    DevBuf walkcnt;                     // unsigned long long[2]: far nodes, near pairs
+    DevBuf walkcnt;                     // unsigned long long[3]: far nodes, near pairs, warp visits
     // sweep
     int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, nmid = 0, lvl0_rows = 0;
     DevBuf split, bigrows, midrows, old;   // row split points, long and medium rows, old attraction
@@ -500,13 +500,23 @@ __global__ void gather_sorted_kernel(const int* __restrict__ perm, const float2*
 }
 
 // ---------------------------------------------------------------------------
-// theta-walk (Algorithm S4), warp-cooperative, Kahan-compensated
+// theta-walk (Algorithm S4), warp-cooperative; KAHAN: every term compensated
 // ---------------------------------------------------------------------------
 
+// s += v, compensated (Kahan) when KAHAN
+template <bool KAHAN>
+__device__ __forceinline__ void acc_add(float& s, float& c, float v) {
+    if (KAHAN)
+        kahan_add(s, c, v);
+    else
+        s += v;
+}
+
+template <bool KAHAN>
 __global__ void __launch_bounds__(256) walk_kernel(
     const int* __restrict__ perm, const float2* __restrict__ spos, const int* __restrict__ first_node,
     int n, const float4* __restrict__ nd_rec, const int2* __restrict__ nd_aux, float theta2,
-    float2* __restrict__ rep, unsigned long long* __restrict__ counts) {
+    float2* __restrict__ rep, unsigned long long* __restrict__ counts, int2* __restrict__ qcounts) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;   // sorted position = query
     const int M = first_node[n];
     const bool active = q < n;
@@ -514,7 +524,7 @@ __global__ void __launch_bounds__(256) walk_kernel(
     const float2 me = active ? spos[q] : make_float2(0.f, 0.f);
     float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
     unsigned next = active ? 0u : (unsigned)M;
-    unsigned far = 0, near = 0;
+    unsigned far = 0, near = 0, visits = 0;   // visits: node records the warp read
     auto visit = [&](unsigned v) {
         const float4 rec = nd_rec[v];
         const int2 aux = nd_aux[v];
@@ -527,8 +537,8 @@ __global__ void __launch_bounds__(256) walk_kernel(
                 const float2 p = cnt == 1 ? make_float2(rec.x, rec.y) : spos[k];
                 float ax = 0.f, ay = 0.f;
                 rep_pair(me.x, me.y, p.x, p.y, ax, ay);
-                kahan_add(sx, cx, ax);
-                kahan_add(sy, cy, ay);
+                acc_add<KAHAN>(sx, cx, ax);
+                acc_add<KAHAN>(sy, cy, ay);
             }
             next = v + 1u;
         } else {
@@ -537,8 +547,8 @@ __global__ void __launch_bounds__(256) walk_kernel(
             const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
             if (rec.z < __fmul_rn(theta2, d2)) {   // acceptance test (Section 3.5)
                 const float w = __fmul_rn(rec.w, rcp_sfu(d2));
-                kahan_add(sx, cx, dx * w);
-                kahan_add(sy, cy, dy * w);
+                acc_add<KAHAN>(sx, cx, dx * w);
+                acc_add<KAHAN>(sy, cy, dy * w);
                 far++;
                 next = (unsigned)aux.x;
             } else {
@@ -549,9 +559,11 @@ __global__ void __launch_bounds__(256) walk_kernel(
     for (;;) {
         const unsigned v = __reduce_min_sync(0xffffffffu, next);
         if (v >= (unsigned)M) break;
+        visits++;
         if (next == v) visit(v);
     }
     if (active) rep[i] = make_float2(sx - cx, sy - cy);
+    if (active && qcounts != nullptr) qcounts[i] = make_int2((int)far, (int)near);   // parity hook
     // interaction counts for reporting
     unsigned long long f = far, nr = near;
     for (int o = 16; o > 0; o >>= 1) {
@@ -561,6 +573,7 @@ __global__ void __launch_bounds__(256) walk_kernel(
     if ((threadIdx.x & 31) == 0 && counts != nullptr) {
         atomicAdd(&counts[0], f);
         atomicAdd(&counts[1], nr);
+        atomicAdd(&counts[2], (unsigned long long)visits);
     }
 }
 
@@ -1027,14 +1040,16 @@ static bl_status bh_ensure(bl_layout* L) {
     BL_TRY(s->lvl.ensure(al, 64 * 4));
     BL_TRY(s->lvl_nodes.ensure(al, (size_t)cap * 4));
     BL_TRY(s->rep.ensure(al, N * sizeof(float2)));
-    BL_TRY(s->walkcnt.ensure(al, 2 * sizeof(unsigned long long)));
+    BL_TRY(s->walkcnt.ensure(al, 4 * sizeof(unsigned long long)));
     s->n = n;
     s->cap_nodes = cap;
     return BL_OK;
 }
 
 // Builds the tree of positions S; leaves codes/perm (sorted) in keys0/vals0.
-static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st) {
+// marks (optional, phase timing): events recorded after the Morton codes and
+// after the sort.
+static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st, cudaEvent_t* marks = nullptr) {
     BHState* s = L->bh;
     const int n = L->g->n;
     const int nbb = std::min(1024, div_up(n, 256));
@@ -1042,6 +1057,7 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st) {
     bbox_final_kernel<<<1, 32, 0, st>>>(s->bpart.as<float4>(), nbb, s->box.as<float>());
     morton_kernel<<<div_up(n, 256), 256, 0, st>>>(S, n, s->box.as<float>(), s->keys0.as<unsigned>(),
                                                   s->vals0.as<int>());
+    if (marks) BL_CUDA_TRY(cudaEventRecord(marks[0], st));
     const int nbs = div_up(n, kSortTile);
     unsigned* kin = s->keys0.as<unsigned>();
     unsigned* kout = s->keys1.as<unsigned>();
@@ -1056,6 +1072,7 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st) {
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
+    if (marks) BL_CUDA_TRY(cudaEventRecord(marks[1], st));
     // after 4 passes the sorted data is back in keys0/vals0
     gather_sorted_kernel<<<div_up(n, 256), 256, 0, st>>>(vin, S, n, s->spos.as<float2>());
     node_count_kernel<<<div_up(n + 1, 256), 256, 0, st>>>(kin, n, s->cnt.as<int>());
@@ -1079,15 +1096,16 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st) {
 
 // repulsion sums of every vertex from the tree of S, neighbours taken out
 static bl_status bh_repulsion(bl_layout* L, const float2* S, float theta, cudaStream_t st,
-                              bool correct = true) {
+                              bool correct = true, int2* qcounts = nullptr) {
     BHState* s = L->bh;
     const int n = L->g->n;
-    BL_CUDA_TRY(cudaMemsetAsync(s->walkcnt.p, 0, 2 * sizeof(unsigned long long), st));
+    BL_CUDA_TRY(cudaMemsetAsync(s->walkcnt.p, 0, 4 * sizeof(unsigned long long), st));
     const float th = theta;
     const float theta2 = th * th;
-    walk_kernel<<<div_up(n, 256), 256, 0, st>>>(s->vals0.as<int>(), s->spos.as<float2>(), s->cnt.as<int>(),
-                                                n, s->nd_rec.as<float4>(), s->nd_aux.as<int2>(), theta2,
-                                                s->rep.as<float2>(), s->walkcnt.as<unsigned long long>());
+    auto walk = kahan_on(L->prm.kahan, n) ? walk_kernel<true> : walk_kernel<false>;
+    walk<<<div_up(n, 256), 256, 0, st>>>(s->vals0.as<int>(), s->spos.as<float2>(), s->cnt.as<int>(), n,
+                                         s->nd_rec.as<float4>(), s->nd_aux.as<int2>(), theta2,
+                                         s->rep.as<float2>(), s->walkcnt.as<unsigned long long>(), qcounts);
     if (correct && !L->prm.repulse_neighbors)
         nbr_correct_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, st>>>(
             L->g->rowptr.as<int>(), L->g->colids.as<int>(), S, n, s->rep.as<float2>());
@@ -1183,6 +1201,28 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     return BL_OK;
 }
 
+// Phase timing (bl_set_phase_timing): per iteration, events around each phase.
+// Main stream: 0 start, 1 Morton codes done, 2 sort done, 3 tree done, 4 walk
+// done, 5 edge pass joined (sweep starts), 6 sweep done, 7 energy done; side
+// stream: 8 edge pass starts, 9 edge pass done.
+constexpr int kPhaseEvents = 10;
+struct PhaseEvents {
+    std::vector<cudaEvent_t> ev;
+    ~PhaseEvents() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    cudaError_t create(int iters) {
+        ev.assign((size_t)iters * kPhaseEvents, nullptr);
+        for (cudaEvent_t& e : ev) {
+            const cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+    cudaEvent_t* at(int t) { return ev.empty() ? nullptr : ev.data() + (size_t)t * kPhaseEvents; }
+};
+
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) {
     BL_TRY(bh_ensure(L));
     BL_TRY(bh_plan(L, BS, st));
@@ -1198,9 +1238,16 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
     if (const char* e = std::getenv("BL_BH_SWEEP_CTAS")) per_sm = std::max(1, std::atoi(e));
     const int G = std::max(1, std::min(occ, per_sm)) * device_sm_count();
     const int nep = std::min(1024, div_up(n, 1024));
+    PhaseEvents pe;
+    if (L->phase_timing) BL_CUDA_TRY(pe.create(iters));
+    auto mark = [&](int t, int q, cudaStream_t on) -> cudaError_t {
+        cudaEvent_t* e = pe.at(t);
+        return e ? cudaEventRecord(e[q], on) : cudaSuccess;
+    };
     for (int t = 0; t < iters; t++) {
         const float2* S = L->pos.as<float2>();
         float2* bnew = L->pos2.as<float2>();
+        BL_CUDA_TRY(mark(t, 0, st));
         // side stream: one pass over the edges (attraction from neighbours that
         // have not moved yet, all rows at once, and the neighbour correction of
         // the tree repulsion) and the sweep's resets; it needs only S and the
@@ -1209,6 +1256,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         const int am = model_exponent(L->prm.energy_model);
         BL_CUDA_TRY(cudaEventRecord(s->ev_fork, st));
         BL_CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        BL_CUDA_TRY(mark(t, 8, s->side));
         edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, s->side>>>(
             L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
             rn, s->old.as<float2>(), s->corr.as<float2>());
@@ -1220,13 +1268,16 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
             edge_pass_big_kernel<<<s->nbig, 1024, 0, s->side>>>(
                 L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
                 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
+        BL_CUDA_TRY(mark(t, 9, s->side));
         BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
         BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
         BL_CUDA_TRY(cudaGetLastError());
         BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
         // main stream: the tree of S and its walk
-        BL_TRY(bh_build(L, S, st));
+        BL_TRY(bh_build(L, S, st, pe.at(t) ? pe.at(t) + 1 : nullptr));
+        BL_CUDA_TRY(mark(t, 3, st));
         BL_TRY(bh_repulsion(L, S, theta, st, false));
+        BL_CUDA_TRY(mark(t, 4, st));
         BL_TRY(layout_reset_sync_words(L, st));
         SweepArgs a{};
         a.rowptr = L->g->rowptr.as<int>();
@@ -1258,6 +1309,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         }
         a.first_level = s->nlevels > 0 ? 1 : 0;
         BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
+        BL_CUDA_TRY(mark(t, 5, st));
         if (a.first_level == 1) {
             const int n0 = s->lvl0_rows;
             level0_kernel<<<std::max(1, std::min(div_up(n0, 256), 8 * device_sm_count())), 256, 0, st>>>(a);
@@ -1265,18 +1317,37 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         void* args[] = {&a};
         BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)dataflow_sweep_kernel, dim3(G),
                                                 dim3(kSweepThreads), args, 0, st));
+        BL_CUDA_TRY(mark(t, 6, st));
         row_energy_kernel<<<nep, 256, 0, st>>>(s->e_row.as<double>(), n, s->epart.as<double>());
         energy_parts_kernel<<<1, 32, 0, st>>>(s->epart.as<double>(), nep, L->energy.as<double>() + t);
         BL_CUDA_TRY(cudaGetLastError());
+        BL_CUDA_TRY(mark(t, 7, st));
         std::swap(L->pos, L->pos2);
         step *= 0.999;
     }
     // interaction counts of the last iteration
-    unsigned long long c[2] = {0, 0};
+    unsigned long long c[3] = {0, 0, 0};
+    int nodes = 0;
     BL_CUDA_TRY(cudaMemcpyAsync(c, s->walkcnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    BL_CUDA_TRY(cudaMemcpyAsync(&nodes, s->cnt.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
     BL_CUDA_TRY(cudaStreamSynchronize(st));
     L->far_nodes = (double)c[0];
     L->near_pairs = (double)c[1];
+    if (pe.at(0)) {   // phase times of this run, summed over its iterations
+        static const int kFrom[kPhaseSlots] = {0, 1, 2, 3, 4, 5, 6, 8, 0};
+        static const int kTo[kPhaseSlots] = {1, 2, 3, 4, 5, 6, 7, 9, 7};
+        double acc[kPhaseSlots] = {};
+        for (int t = 0; t < iters; t++)
+            for (int q = 0; q < kPhaseSlots; q++) {
+                float ms = 0.f;
+                BL_CUDA_TRY(cudaEventElapsedTime(&ms, pe.at(t)[kFrom[q]], pe.at(t)[kTo[q]]));
+                acc[q] += ms;
+            }
+        for (int q = 0; q < kPhaseSlots; q++) L->phase_ms[q] = acc[q];
+        L->phase_nodes = nodes;
+        L->phase_visits = (double)c[2];
+        L->phase_iters = iters;
+    }
     return BL_OK;
 }
 
@@ -1295,6 +1366,14 @@ bl_status bh_debug_forces(bl_layout* L, float theta, float2* f_out, cudaStream_t
     BL_CUDA_TRY(cudaStreamSynchronize(st));
     L->far_nodes = (double)c[0];
     L->near_pairs = (double)c[1];
+    return BL_OK;
+}
+
+bl_status bh_debug_counts(bl_layout* L, float theta, int2* qcounts, cudaStream_t st) {
+    BL_TRY(bh_ensure(L));
+    const float2* S = L->pos.as<float2>();
+    BL_TRY(bh_build(L, S, st));
+    BL_TRY(bh_repulsion(L, S, theta, st, false, qcounts));
     return BL_OK;
 }
 

@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     const bool rn = prm.repulse_neighbors != 0;
     const float invK = prm.invK, negRK2 = prm.negRK2;
     const int am = prm.am;
+    const bool kahan = prm.kahan != 0;
     float2* const buf0 = tk.pos;
     float2* const buf1 = tk.pos_alt;
 
@@ -245,8 +246,13 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 rep_pair(xi, yi, pc.x, pc.y, ax, ay);
             }
             if (need[m]) {
-                kahan_add(sx[m], cx[m], ax);
-                kahan_add(sy[m], cy[m], ay);
+                if (kahan) {   // compensated across the row's column tiles
+                    kahan_add(sx[m], cx[m], ax);
+                    kahan_add(sy[m], cy[m], ay);
+                } else {
+                    sx[m] += ax;
+                    sy[m] += ay;
+                }
             }
         }
     };
@@ -456,8 +462,13 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 }
                 float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
                 if (kprev >= 0) {
-                    kahan_add(sxr, cxr, rxs);
-                    kahan_add(syr, cyr, rys);
+                    if (kahan) {
+                        kahan_add(sxr, cxr, rxs);
+                        kahan_add(syr, cyr, rys);
+                    } else {
+                        sxr += rxs;
+                        syr += rys;
+                    }
                 }
                 const float fx = fmaf(negRK2, (sxr - cxr) - qx, ax);
                 const float fy = fmaf(negRK2, (syr - cyr) - qy, ay);

@@ -36,6 +36,7 @@ struct ClusterTask {
     double step0;
     float invK, negRK2;
     int rn, am;
+    int kahan;          // 1: each lane's strided repulsion sum compensated
     int csr_smem;       // CSR copied into shared memory
     int gs;             // threads per row group (multiple of 32)
 };
@@ -102,10 +103,24 @@ __global__ void __launch_bounds__(kClThreads, 1) exact_cluster_kernel(ClusterTas
                 float2 me = make_float2(0.f, 0.f);
                 if (have) {
                     me = P[i];
+                    if (tk.kahan) {   // every term compensated (uniform branch)
+                        float cx = 0.f, cy = 0.f;
 #pragma unroll 4
-                    for (int j = tg; j < n; j += GS) {
-                        const float2 p = P[j];
-                        rep_pair(me.x, me.y, p.x, p.y, rx, ry);   // j == i gives 0
+                        for (int j = tg; j < n; j += GS) {
+                            const float2 p = P[j];
+                            float tx = 0.f, ty = 0.f;
+                            rep_pair(me.x, me.y, p.x, p.y, tx, ty);   // j == i gives 0
+                            kahan_add(rx, cx, tx);
+                            kahan_add(ry, cy, ty);
+                        }
+                        rx -= cx;
+                        ry -= cy;
+                    } else {
+#pragma unroll 4
+                        for (int j = tg; j < n; j += GS) {
+                            const float2 p = P[j];
+                            rep_pair(me.x, me.y, p.x, p.y, rx, ry);   // j == i gives 0
+                        }
                     }
                     const int e1 = rowptr[i + 1];
                     for (int e = rowptr[i] + tg; e < e1; e += GS)
@@ -200,7 +215,7 @@ bool cluster_engine_fits(int n, int BS, int64_t nnz) {
 }
 
 bl_status cluster_run(const int* rowptr, const int* colids, int64_t nnz, int n, float2* pos, int iters, int BS,
-                      double step0, float invK, float negRK2, int rn, int am, double* e_iter_buf,
+                      double step0, float invK, float negRK2, int rn, int am, int kahan, double* e_iter_buf,
                       double* energy, cudaStream_t st, int* C_out) {
     const bool csr = (size_t)((n + 1) + nnz) * 4 + (size_t)n * 8 + (size_t)4 * BS * 8 + 4096 <= 200 * 1024;
     // threads per row group: the minibatch's rows per CTA spread over the CTA
@@ -229,6 +244,7 @@ bl_status cluster_run(const int* rowptr, const int* colids, int64_t nnz, int n, 
     tk.negRK2 = negRK2;
     tk.rn = rn;
     tk.am = am;
+    tk.kahan = kahan;
     tk.csr_smem = csr ? 1 : 0;
     tk.gs = gs;
     BL_CUDA_TRY(cudaFuncSetAttribute(exact_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

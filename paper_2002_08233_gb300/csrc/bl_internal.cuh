@@ -117,12 +117,17 @@ struct bl_layout {
     int trace_steps = 0;                // phase trace of the next run (0 = off)
     bl::DevBuf trace;                   // uint64 timestamps
     int64_t trace_count = 0;            // entries written by the last traced run
+    int phase_timing = 0;               // Barnes-Hut phase events on (bl_set_phase_timing)
+    double phase_ms[9] = {};            // phase times of the last timed BH run (bl_get_phase_times)
+    double phase_nodes = 0.0, phase_visits = 0.0;
+    int64_t phase_iters = 0;
 };
 
 namespace bl {
 
 // device status word values are bl_status codes
 constexpr int kMaxBatch = 8192;
+constexpr int kPhaseSlots = 9;    // Barnes-Hut phase times (bl_get_phase_times)
 constexpr int kTraceSlots = 12;   // timestamps per CTA and step in a phase trace
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 
@@ -151,6 +156,7 @@ struct ExactParams {
     float negRK2;        // -R K^2
     int repulse_neighbors;
     int am;              // attraction exponent a of the (a,-1) model
+    int kahan;           // 1: compensated repulsion sums across column tiles, 0: plain
     int* status;         // device status word
     unsigned* bar;       // step counter (one arrival per CTA per step)
 };
@@ -179,6 +185,11 @@ bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, 
 // Barnes-Hut iterations of one layout (bl_bh.cu); the caller updates L's counters.
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st);
 
+// Compensated (Kahan) FP32 repulsion sums: bl_force_params.kahan = 1 always, 0
+// never, < 0 from kKahanAutoN vertices on.
+constexpr int64_t kKahanAutoN = 1000000;
+inline bool kahan_on(int kahan, int64_t n) { return kahan > 0 || (kahan < 0 && n >= kKahanAutoN); }
+
 // Attraction exponent a of an energy model (bl_energy_model): FR 2, FA 1, LinLog 0, A3 3.
 inline int model_exponent(int energy_model) {
     static const int kA[4] = {2, 1, 0, 3};
@@ -192,7 +203,7 @@ bool cluster_engine_fits(int n, int BS, int64_t nnz);
 // `iters` iterations of positions pos (updated in place); e_iter_buf holds
 // iters x 16 doubles; energy (may be null) receives the per-iteration energies.
 bl_status cluster_run(const int* rowptr, const int* colids, int64_t nnz, int n, float2* pos, int iters, int BS,
-                      double step0, float invK, float negRK2, int rn, int am, double* e_iter_buf,
+                      double step0, float invK, float negRK2, int rn, int am, int kahan, double* e_iter_buf,
                       double* energy, cudaStream_t st, int* C_out);
 
 // Whole-GPU exact run of one layout (bl_runtime.cu); the caller updates L's counters.

@@ -9,7 +9,9 @@
 // file-scope device array instead of allocating it. Every GPU that loads the
 // library holds that array (about 2 MiB) until the process exits.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "bl_internal.cuh"
@@ -29,24 +31,58 @@ constexpr size_t kNoAllocBytes =
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
+struct ScratchEntry {
+    void* addr = nullptr;
+    unsigned long long ctx = 0;   // id of the context the address belongs to
+};
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+ScratchEntry g_scratch[kMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once per
-// device with that device current.
+// Unique id of the calling thread's current context (cuCtxGetCurrent +
+// cuCtxGetId, reached through the runtime's driver entry points so the library
+// does not link the driver library), or 0 when there is none or it is unknown.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+    unsigned long long id = 0;
+    return get_id(c, &id) == CUDA_SUCCESS ? id : 0;
+}
+
+// Device address of the scratch array on the current device. It is looked up
+// with the device current on the first call, and again whenever the device's
+// context has changed since (after a cudaDeviceReset the old address is stale).
 bl_status scratch_address(void** out) {
     int dev = 0;
     BL_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices)
         return set_error(BL_EINVAL, "bl_layout_run_noalloc: device index out of range");
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (g_scratch_addr[dev] == nullptr) {
+    ScratchEntry& ent = g_scratch[dev];
+    if (ent.addr == nullptr || ctx == 0 || ctx != ent.ctx) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(scratch)");
-        g_scratch_addr[dev] = p;
+        ent.addr = p;
+        ent.ctx = current_context_id();   // the lookup made the context current if it was not
     }
-    *out = g_scratch_addr[dev];
+    *out = ent.addr;
     return BL_OK;
 }
 
@@ -68,10 +104,12 @@ extern "C" bl_status bl_layout_run_noalloc(int32_t n, const int32_t* d_rowptr, c
         return set_error(BL_EINVAL, "bl_layout_run_noalloc: batch must be in [1, 8192]");
     bl_force_params p{1.0f, 1.0f, 0, -1, BL_MODEL_FR};
     if (params) p = *params;
-    if (!(p.K > 0.0f) || !(p.R > 0.0f))
-        return set_error(BL_EINVAL, "bl_layout_run_noalloc: K and R must be positive");
+    if (!(p.K > 0.0f) || !(p.R > 0.0f) || !std::isfinite(p.K) || !std::isfinite(p.R))
+        return set_error(BL_EINVAL, "bl_layout_run_noalloc: K and R must be positive and finite");
     if (p.energy_model < 0 || p.energy_model > 3)
         return set_error(BL_EINVAL, "bl_layout_run_noalloc: energy_model must be 0..3");
+    if (p.kahan < -1 || p.kahan > 1)
+        return set_error(BL_EINVAL, "bl_layout_run_noalloc: kahan must be -1, 0 or 1");
     if (iters == 0) return BL_OK;
     ExactPlan plan;
     BL_TRY(exact_plan(n, batch, 0, 0, &plan));
@@ -105,6 +143,7 @@ extern "C" bl_status bl_layout_run_noalloc(int32_t n, const int32_t* d_rowptr, c
     prm.negRK2 = -p.R * p.K * p.K;
     prm.repulse_neighbors = p.repulse_neighbors;
     prm.am = model_exponent(p.energy_model);
+    prm.kahan = kahan_on(p.kahan, n) ? 1 : 0;
     prm.status = reinterpret_cast<int*>(sc);
     prm.bar = reinterpret_cast<unsigned*>(sc + 64);
     BL_TRY(exact_launch(plan, tk, prm, st));

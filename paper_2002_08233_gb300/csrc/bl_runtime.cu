@@ -125,16 +125,13 @@ unsigned* layout_barrier_word(bl_layout* L) {
 // BH engine entry points (bl_bh.cu)
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st);
 bl_status bh_debug_forces(bl_layout* L, float theta, float2* f_out, cudaStream_t st);
+bl_status bh_debug_counts(bl_layout* L, float theta, int2* qcounts, cudaStream_t st);
 bl_status bh_debug_tree(bl_layout* L, uint32_t* codes, int32_t* perm, int32_t* first,
                         int32_t* count, int32_t* level, int32_t* skip, float* sumx, float* sumy,
                         int64_t cap, int64_t* nnodes, float* box, cudaStream_t st);
 // quality (bl_quality.cu)
 bl_status quality_run(bl_layout* L, int32_t nsources, int32_t nqueries, uint64_t seed,
                       double* out, int64_t cap, cudaStream_t st);
-
-static bool use_kahan(const bl_layout* L) {
-    return L->prm.kahan > 0 || (L->prm.kahan < 0 && L->g->n >= (1 << 20));
-}
 
 // Small graphs whose minibatch chain dominates run on one thread-block cluster
 // (BL_EXACT_ENGINE=grid|cluster forces an engine).
@@ -156,7 +153,8 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
         return cluster_run(L->g->rowptr.as<int>(), L->g->colids.as<int>(), L->g->nnz, n, L->pos.as<float2>(),
                            iters, BS, s, 1.0f / L->prm.K, -L->prm.R * L->prm.K * L->prm.K,
                            L->prm.repulse_neighbors, model_exponent(L->prm.energy_model),
-                           L->epart.as<double>(), L->energy.as<double>(), st, nullptr);
+                           kahan_on(L->prm.kahan, n) ? 1 : 0, L->epart.as<double>(), L->energy.as<double>(),
+                           st, nullptr);
     }
     ExactPlan plan;
     BL_TRY(exact_plan(n, BS, 0, 0, &plan));
@@ -195,6 +193,7 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     prm.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
     prm.repulse_neighbors = L->prm.repulse_neighbors;
     prm.am = model_exponent(L->prm.energy_model);
+    prm.kahan = kahan_on(L->prm.kahan, n) ? 1 : 0;
     prm.status = static_cast<int*>(L->status.p);
     prm.bar = layout_barrier_word(L);
     BL_TRY(layout_reset_sync_words(L, st));
@@ -236,6 +235,7 @@ bl_status layout_create(const bl_graph* g, const float* xy, uint64_t seed, int64
         return set_error(BL_EINVAL, "bl_layout_init: K and R must be positive and finite");
     if (p.energy_model < 0 || p.energy_model > 3)
         return set_error(BL_EINVAL, "bl_layout_init: energy_model must be 0..3");
+    if (p.kahan < -1 || p.kahan > 1) return set_error(BL_EINVAL, "bl_layout_init: kahan must be -1, 0 or 1");
     bl_layout* L = new bl_layout();
     L->g = g;
     L->prm = p;
@@ -645,6 +645,41 @@ bl_status bl_debug_forces(bl_layout* L, bl_mode mode, float theta, int32_t lo, i
     BL_CUDA_TRY(cudaMemcpyAsync(f_out, f + lo, (size_t)(hi - lo) * sizeof(float2), cudaMemcpyDeviceToHost, st));
     BL_CUDA_TRY(cudaStreamSynchronize(st));
     return check_stream_status(L);
+}
+
+bl_status bl_debug_bh_counts(bl_layout* L, float theta, int32_t* far, int32_t* near, int64_t cap) {
+    if (!L || !far || !near) return set_error(BL_EINVAL, "bl_debug_bh_counts: NULL argument");
+    const int n = L->g->n;
+    if (cap < n) return set_error(BL_EINVAL, "bl_debug_bh_counts: output too small");
+    if (!(theta >= 0.0f)) return set_error(BL_EINVAL, "bl_debug_bh_counts: theta must be >= 0");
+    cudaStream_t st = current_stream();
+    BL_TRY(L->scratch.ensure(L->alloc, (size_t)n * sizeof(int2)));
+    int2* q = L->scratch.as<int2>();
+    BL_TRY(bh_debug_counts(L, theta, q, st));
+    std::vector<int2> h((size_t)n);
+    BL_CUDA_TRY(cudaMemcpyAsync(h.data(), q, (size_t)n * sizeof(int2), cudaMemcpyDeviceToHost, st));
+    BL_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; i++) {
+        far[i] = h[i].x;
+        near[i] = h[i].y;
+    }
+    return BL_OK;
+}
+
+bl_status bl_set_phase_timing(bl_layout* L, int32_t on) {
+    if (!L) return set_error(BL_EINVAL, "bl_set_phase_timing: NULL layout");
+    L->phase_timing = on != 0;
+    return BL_OK;
+}
+
+bl_status bl_get_phase_times(const bl_layout* L, double* out, int64_t cap) {
+    if (!L || !out) return set_error(BL_EINVAL, "bl_get_phase_times: NULL argument");
+    if (cap < kPhaseSlots + 3) return set_error(BL_EINVAL, "bl_get_phase_times: output needs 12 doubles");
+    for (int q = 0; q < kPhaseSlots; q++) out[q] = L->phase_ms[q];
+    out[kPhaseSlots] = L->phase_nodes;
+    out[kPhaseSlots + 1] = L->phase_visits;
+    out[kPhaseSlots + 2] = (double)L->phase_iters;
+    return BL_OK;
 }
 
 bl_status bl_set_trace(bl_layout* L, int32_t max_steps) {

@@ -4,6 +4,9 @@ Force error of vertex i: |f_gpu - f_oracle| / sum_j |t_ij|, the oracle's sum of
 the magnitudes of the terms that make up f(i,c). Repulsion sums cancel, so this
 measures the FP32 error against the size of what was summed.
 """
+import json
+import os
+
 import numpy as np
 
 TOL_FORCE_EXACT = 1e-5
@@ -44,3 +47,38 @@ def oracle_sensitivity(g, xy, iters, batch, trials=3, seed=1, **kw):
 
 def position_tolerance(base_tol, sensitivity, factor=4.0):
     return max(base_tol, factor * sensitivity)
+
+
+def log_parity(kind, **fields):
+    """Appends one JSON line {kind, fields...} to the file named by BL_PARITY_LOG
+    (nothing when it is unset): the errors, spreads and tolerances a parity test
+    applied, so a reader can see how close a passing gate was."""
+    path = os.environ.get("BL_PARITY_LOG")
+    if not path:
+        return
+    rec = {"kind": kind}
+    for k, v in fields.items():
+        rec[k] = v.item() if hasattr(v, "item") and np.ndim(v) == 0 else v
+    with open(path, "a") as fh:
+        fh.write(json.dumps(rec, default=float) + "\n")
+
+
+def assert_positions(label, x_gpu, x_ref, base_tol, sensitivity, factor=4.0, scale=1.0):
+    """Positions parity with the tolerance of the one-ulp reading: error <=
+    scale * max(base_tol, factor * S). The message and the parity log carry the
+    error, S and the tolerance that was applied."""
+    err = float(position_error(x_gpu, x_ref))
+    tol = scale * position_tolerance(base_tol, sensitivity, factor)
+    log_parity("positions", label=str(label), err=err, sensitivity=float(sensitivity),
+               base_tol=base_tol, tol=tol)
+    assert err <= tol, (f"{label}: position error {err:.3e} > tolerance {tol:.3e} (base {base_tol:.0e}, "
+                        f"oracle one-ulp sensitivity S = {float(sensitivity):.3e})")
+    return err
+
+
+def assert_forces(label, f_gpu, f_ref, mag, tol):
+    """Condition-aware force parity: max_i |f_gpu - f_oracle| / sum_j |t_ij| <= tol."""
+    err = float(force_error(f_gpu, f_ref, mag).max()) if len(mag) else 0.0
+    log_parity("forces", label=str(label), err=err, tol=tol)
+    assert err <= tol, f"{label}: force error {err:.3e} > tolerance {tol:.0e}"
+    return err

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_2002_08233_gb300 import synth
-from helpers import TOL_POS_EXACT, oracle_sensitivity, position_error, position_tolerance
+from helpers import TOL_POS_EXACT, oracle_sensitivity, position_error, assert_positions
 
 pytestmark = pytest.mark.gpu
 
@@ -56,8 +56,7 @@ def test_one_iteration_matches_oracle(core, bs):
         xy = synth.uniform_positions(g.n, int(sd))
         xr, sens = oracle_sensitivity(g, xy, 1, bs, nthreads=NCPU)
         _, er = oracle.run(g, xy, iters=1, batch=bs, nthreads=NCPU)
-        err = position_error(L.positions(), xr)
-        assert err <= position_tolerance(TOL_POS_EXACT, sens), (g.name, g.n, err, sens)
+        assert_positions((g.name, g.n), L.positions(), xr, TOL_POS_EXACT, sens)
         assert L.energy_history()[0] == pytest.approx(er[0], rel=1e-4)
 
 
@@ -68,8 +67,7 @@ def test_three_iterations_match_oracle(core):
     for g, L, sd in zip(gs, Ls, seeds):
         xy = synth.uniform_positions(g.n, int(sd))
         xr, sens = oracle_sensitivity(g, xy, 3, 64, nthreads=NCPU)
-        err = position_error(L.positions(), xr)
-        assert err <= position_tolerance(TOL_POS_EXACT, sens), (g.name, err, sens)
+        assert_positions(g.name, L.positions(), xr, TOL_POS_EXACT, sens)
         assert L.stats()["iterations"] == 3
 
 
@@ -134,7 +132,7 @@ def test_graph_above_fair_share_runs_on_whole_gpu(core):
     for g, L, sd in zip(gs, Ls, seeds):
         xy = synth.uniform_positions(g.n, int(sd))
         xr, sens = oracle_sensitivity(g, xy, 1, 256, nthreads=NCPU)
-        assert position_error(L.positions(), xr) <= position_tolerance(TOL_POS_EXACT, sens), g.n
+        assert_positions(("mixed", g.n), L.positions(), xr, TOL_POS_EXACT, sens)
 
 
 def test_degenerate_graphs(core):
@@ -185,5 +183,4 @@ def test_full_mix_sampled_parity(core):
         g = gs[k]
         xy = synth.uniform_positions(g.n, int(seeds[k]))
         xr, sens = oracle_sensitivity(g, xy, 1, 64, trials=1, nthreads=NCPU)
-        err = position_error(Ls[k].positions(), xr)
-        assert err <= position_tolerance(TOL_POS_EXACT, sens), (k, g.n, err, sens)
+        assert_positions(("sample", k, g.n), Ls[k].positions(), xr, TOL_POS_EXACT, sens)

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2002_08233_gb300 import synth
-from helpers import TOL_POS_EXACT, oracle_sensitivity, position_error, position_tolerance
+from helpers import TOL_POS_EXACT, oracle_sensitivity, assert_positions
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +48,7 @@ def test_one_iteration_matches_oracle(core, cluster_engine, name, maker, bs):
     L.run(1, bs, "exact")
     xr, sens = oracle_sensitivity(g, xy, 1, bs, nthreads=NCPU)
     _, er = oracle.run(g, xy, iters=1, batch=bs, nthreads=NCPU)
-    assert position_error(L.positions(), xr) <= position_tolerance(TOL_POS_EXACT, sens), name
+    assert_positions(name, L.positions(), xr, TOL_POS_EXACT, sens)
     assert L.energy_history()[0] == pytest.approx(er[0], rel=1e-4)
 
 
@@ -59,7 +59,7 @@ def test_three_iterations_with_models(core, cluster_engine):
         L = core.Layout(core.Graph(g), xy=xy, model=model, K=0.9, R=1.2)
         L.run(3, 64, "exact")
         xr, sens = oracle_sensitivity(g, xy, 3, 64, a=a, K=0.9, R=1.2, nthreads=NCPU)
-        assert position_error(L.positions(), xr) <= position_tolerance(TOL_POS_EXACT, sens), model
+        assert_positions(model, L.positions(), xr, TOL_POS_EXACT, sens)
 
 
 def test_split_runs_equal_one_run(core, cluster_engine):
@@ -87,4 +87,5 @@ def test_cluster_and_grid_engines_agree(core):
         finally:
             os.environ.pop("BL_EXACT_ENGINE", None)
     _, sens = oracle_sensitivity(g, xy, 2, 128, nthreads=NCPU)
-    assert position_error(out["cluster"], out["grid"].astype(np.float64)) <= 2 * position_tolerance(TOL_POS_EXACT, sens)
+    assert_positions("cluster vs grid engine", out["cluster"], out["grid"].astype(np.float64), TOL_POS_EXACT,
+                     sens, scale=2.0)

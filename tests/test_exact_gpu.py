@@ -7,8 +7,8 @@ import pytest
 
 import oracle
 from paper_2002_08233_gb300 import synth
-from helpers import (TOL_FORCE_EXACT, TOL_POS_EXACT, force_error, oracle_sensitivity,
-                     position_error, position_tolerance)
+from helpers import (TOL_FORCE_EXACT, TOL_POS_EXACT, oracle_sensitivity, assert_positions,
+                     assert_forces)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,8 +54,7 @@ def test_snapshot_forces_match_oracle(core, name, maker, seed, rn):
     _, L = _layout(core, g, xy, repulse_neighbors=rn)
     f = L.debug_forces("exact")
     ref, mag = oracle.forces(g, xy.astype(np.float64), repulse_neighbors=rn)
-    err = force_error(f, ref, mag)
-    assert err.max() <= TOL_FORCE_EXACT, (name, err.max())
+    assert_forces((name, rn), f, ref, mag, TOL_FORCE_EXACT)
 
 
 def test_snapshot_forces_nondefault_K_R(core):
@@ -64,7 +63,7 @@ def test_snapshot_forces_nondefault_K_R(core):
     _, L = _layout(core, g, xy, K=0.7, R=2.5)
     f = L.debug_forces("exact")
     ref, mag = oracle.forces(g, xy.astype(np.float64), K=0.7, R=2.5)
-    assert force_error(f, ref, mag).max() <= TOL_FORCE_EXACT
+    assert_forces("K=0.7 R=2.5", f, ref, mag, TOL_FORCE_EXACT)
 
 
 def test_snapshot_forces_evolved_layout(core):
@@ -77,7 +76,7 @@ def test_snapshot_forces_evolved_layout(core):
     _, L = _layout(core, g, xe, start_iter=30)
     f = L.debug_forces("exact")
     ref, mag = oracle.forces(g, xe.astype(np.float64))
-    assert force_error(f, ref, mag).max() <= TOL_FORCE_EXACT
+    assert_forces("evolved layout", f, ref, mag, TOL_FORCE_EXACT)
 
 
 ITER_CASES = [
@@ -100,9 +99,7 @@ def test_one_iteration_positions_match_oracle(core, engine, name, maker, bs, see
     xg = L.positions()
     xr, sens = oracle_sensitivity(g, xy, 1, bs, nthreads=NCPU)
     _, er = oracle.run(g, xy, iters=1, batch=bs, nthreads=NCPU)
-    err = position_error(xg, xr)
-    tol = position_tolerance(TOL_POS_EXACT, sens)
-    assert err <= tol, (name, err, sens)
+    assert_positions(name, xg, xr, TOL_POS_EXACT, sens)
     eg = L.energy_history()
     assert eg.shape == (1,)
     assert eg[0] == pytest.approx(er[0], rel=1e-4)
@@ -144,7 +141,7 @@ def test_step_schedule_continues_across_runs(core):
     assert st["iterations"] == 20
     assert st["step"] == pytest.approx(0.999 ** 20, rel=1e-12)
     xr, sens = oracle_sensitivity(g, xy, 3, 64, start_iter=17, nthreads=NCPU)
-    assert position_error(L.positions(), xr) <= position_tolerance(TOL_POS_EXACT, sens)
+    assert_positions("continues at t=17", L.positions(), xr, TOL_POS_EXACT, sens)
 
 
 def test_every_vertex_moves_by_step(core):
@@ -209,7 +206,7 @@ def test_ba65536_sampled_forces(core, ba65k):
         lo, hi = int(b) * 256, int(b) * 256 + 256
         f = L.debug_forces("exact", lo=lo, hi=hi)
         ref, mag = oracle.forces(g, xy.astype(np.float64), lo=lo, hi=hi)
-        assert force_error(f, ref, mag).max() <= TOL_FORCE_EXACT
+        assert_forces(("ba65536", lo), f, ref, mag, TOL_FORCE_EXACT)
 
 
 def test_ba65536_one_iteration(core, ba65k):
@@ -219,10 +216,9 @@ def test_ba65536_one_iteration(core, ba65k):
     _, L = _layout(core, g, xy)
     L.run(1, 256, "exact")
     xr, er = oracle.run(g, xy, iters=1, batch=256, nthreads=NCPU)
-    err = position_error(L.positions(), xr)
     # one perturbed oracle run (each costs a full 4.3e9-pair iteration)
     _, sens = oracle_sensitivity(g, xy, 1, 256, trials=1, nthreads=NCPU)
-    assert err <= position_tolerance(TOL_POS_EXACT, sens), (err, sens)
+    assert_positions("ba65536 one iteration", L.positions(), xr, TOL_POS_EXACT, sens)
     assert L.energy_history()[0] == pytest.approx(er[0], rel=1e-4)
 
 

@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2002_08233_gb300 import synth
 from helpers import (TOL_FORCE_BH, TOL_FORCE_EXACT, TOL_POS_BH, TOL_POS_EXACT, force_error,
-                     oracle_sensitivity, position_error, position_tolerance)
+                     oracle_sensitivity, assert_positions, assert_forces)
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +36,7 @@ def test_snapshot_forces(core, model, a, mode):
                              mode=oracle.EXACT if mode == "exact" else oracle.BH, theta=0.6,
                              nthreads=NCPU)
     tol = TOL_FORCE_EXACT if mode == "exact" else TOL_FORCE_BH
-    assert force_error(f, ref, mag).max() <= tol
+    assert_forces((model, mode), f, ref, mag, tol)
 
 
 @pytest.mark.parametrize("model,a", MODELS)
@@ -60,7 +60,7 @@ def test_one_iteration(core, model, a, engine):
     mode = oracle.BH if engine == "bh" else oracle.EXACT
     xr, sens = oracle_sensitivity(g, xy, 1, 64, mode=mode, theta=1.2, a=a, nthreads=NCPU)
     base = TOL_POS_BH if engine == "bh" else TOL_POS_EXACT
-    assert position_error(L.positions(), xr) <= position_tolerance(base, sens)
+    assert_positions((model, engine), L.positions(), xr, base, sens)
 
 
 @pytest.mark.parametrize("model,a", MODELS)
