@@ -13,7 +13,10 @@ ulp changes the oracle's own final stress by up to ~15% on grids and trees
 (different local minima), while on random graphs it stays within ~0.2%. Each run
 is therefore held to max(2%, 2x the oracle's own one-ulp spread on that input),
 which is the strict 2% wherever the run is well-conditioned; on the chaotic
-families the ensemble over 16 seeds must show no systematic shift. Every assert
+families the ensemble over 16 seeds must show no systematic shift. NP is a mean of
+Jaccard ratios of small neighbour counts: on random graphs (NP ~ 0.002) the
+whole layout has under a hundred hits, so NP also gets the floor of two standard
+errors of that count, 2/sqrt(hits). Every assert
 message carries the error, the spread and the tolerance applied; with
 BL_PARITY_LOG set they are also appended to that file as JSON lines."""
 import os
@@ -42,12 +45,14 @@ def _q(g, xy):
     return oracle.stress(g, xy)[0], oracle.neighborhood_preservation(g, xy)[0]
 
 
-def _oracle_with_spread(g, xy0, iters, bs, mode=oracle.EXACT, trials=3):
-    """The oracle's layout and quality, and how far its quality moves when every
-    start coordinate moves by one ulp."""
+def _oracle_with_spread(g, xy0, iters, bs, mode=oracle.EXACT, trials=5):
+    """The oracle's layout and quality, how far its quality moves when every start
+    coordinate moves by one ulp, and its NP hit count (intersections summed over
+    the queries)."""
     kw = dict(iters=iters, batch=bs, mode=mode, theta=1.2, nthreads=NCPU)
     xr, _ = oracle.run(g, xy0, **kw)
-    s0, n0 = _q(g, xr)
+    s0 = oracle.stress(g, xr)[0]
+    n0, _, hits = oracle.neighborhood_preservation(g, xr)
     rng = np.random.default_rng(12345)
     ds = dn = 0.0
     for _ in range(trials):
@@ -56,7 +61,7 @@ def _oracle_with_spread(g, xy0, iters, bs, mode=oracle.EXACT, trials=3):
         s, n_ = _q(g, xp)
         ds = max(ds, abs(s / s0 - 1))
         dn = max(dn, abs(n_ / n0 - 1) if n0 > 0 else 0.0)
-    return xr, s0, n0, ds, dn
+    return xr, s0, n0, ds, dn, hits
 
 
 def _gpu_run(core, G, xy0, iters, bs, engine):
@@ -104,9 +109,9 @@ def test_whole_run_quality_matches_oracle(core, name, maker, iters, bs, engines,
     g = maker()
     xy0 = synth.uniform_positions(g.n, seed)
     mode = oracle.BH if engines == ("bh",) else oracle.EXACT
-    xr, s_r, np_r, ds, dn = _oracle_with_spread(g, xy0, iters, bs, mode)
+    xr, s_r, np_r, ds, dn, hits = _oracle_with_spread(g, xy0, iters, bs, mode)
     tol_s = max(0.02, 2 * ds)
-    tol_np = max(0.02, 2 * dn)
+    tol_np = max(0.02, 2 * dn, 2 / np.sqrt(max(hits, 1)))
     G = core.Graph(g)
     for engine in engines:
         L = _gpu_run(core, G, xy0, iters, bs, engine)
@@ -115,7 +120,7 @@ def test_whole_run_quality_matches_oracle(core, name, maker, iters, bs, engines,
         info = dict(case=name, seed=seed, engine=engine, n=g.n, iters=iters, batch=bs,
                     stress_gpu=s_g, stress_oracle=s_r, stress_err=es, stress_spread=ds,
                     stress_tol=tol_s, np_gpu=np_g, np_oracle=np_r, np_err=en, np_spread=dn,
-                    np_tol=tol_np)
+                    np_hits=hits, np_tol=tol_np)
         log_parity("e2e_quality", **info)
         assert es <= tol_s, info
         assert en <= tol_np, info
