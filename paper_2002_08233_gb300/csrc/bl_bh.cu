@@ -75,6 +75,11 @@ struct BHState {
     // the edge pass runs on a side stream while the tree is built and walked
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the iteration's critical path runs on a highest-priority stream forked from and
+    // joined back to the caller's, so the edge pass (default priority) does not
+    // hold SMs the tree build and sweep are waiting for
+    cudaStream_t hi = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 void bh_state_free(BHState* s) {
@@ -90,6 +95,9 @@ void bh_state_free(BHState* s) {
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->side) cudaStreamDestroy(s->side);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    if (s->hi) cudaStreamDestroy(s->hi);
     delete s;
 }
 
@@ -1015,6 +1023,13 @@ static bl_status bh_ensure(bl_layout* L) {
     if (!s->side) BL_CUDA_TRY(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     if (!s->ev_fork) BL_CUDA_TRY(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
     if (!s->ev_join) BL_CUDA_TRY(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+    if (!s->hi) {
+        int lo_prio = 0, hi_prio = 0;
+        BL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+        BL_CUDA_TRY(cudaStreamCreateWithPriority(&s->hi, cudaStreamNonBlocking, hi_prio));
+    }
+    if (!s->ev_in) BL_CUDA_TRY(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+    if (!s->ev_out) BL_CUDA_TRY(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
     if (s->n == n && s->cap_nodes > 0) return BL_OK;
     const Allocator& al = L->alloc;
     const size_t N = (size_t)n;
@@ -1223,9 +1238,9 @@ struct PhaseEvents {
     cudaEvent_t* at(int t) { return ev.empty() ? nullptr : ev.data() + (size_t)t * kPhaseEvents; }
 };
 
-bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) {
+bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t caller) {
     BL_TRY(bh_ensure(L));
-    BL_TRY(bh_plan(L, BS, st));
+    BL_TRY(bh_plan(L, BS, caller));
     BHState* s = L->bh;
     const int n = L->g->n;
     BL_TRY(L->pos2.ensure(L->alloc, (size_t)n * sizeof(float2)));
@@ -1238,6 +1253,14 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
     if (const char* e = std::getenv("BL_BH_SWEEP_CTAS")) per_sm = std::max(1, std::atoi(e));
     const int G = std::max(1, std::min(occ, per_sm)) * device_sm_count();
     const int nep = std::min(1024, div_up(n, 1024));
+    // st: the stream of the iteration's critical path (BL_BH_PRIORITY=0: the caller's)
+    const char* pe_env = std::getenv("BL_BH_PRIORITY");
+    const bool use_hi = !(pe_env && pe_env[0] == '0');
+    cudaStream_t st = use_hi ? s->hi : caller;
+    if (use_hi) {
+        BL_CUDA_TRY(cudaEventRecord(s->ev_in, caller));
+        BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_in, 0));
+    }
     PhaseEvents pe;
     if (L->phase_timing) BL_CUDA_TRY(pe.create(iters));
     auto mark = [&](int t, int q, cudaStream_t on) -> cudaError_t {
@@ -1324,6 +1347,10 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st) 
         BL_CUDA_TRY(mark(t, 7, st));
         std::swap(L->pos, L->pos2);
         step *= 0.999;
+    }
+    if (use_hi) {   // the caller's stream continues after the iterations
+        BL_CUDA_TRY(cudaEventRecord(s->ev_out, st));
+        BL_CUDA_TRY(cudaStreamWaitEvent(caller, s->ev_out, 0));
     }
     // interaction counts of the last iteration
     unsigned long long c[3] = {0, 0, 0};

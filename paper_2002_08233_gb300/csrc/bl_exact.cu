@@ -28,6 +28,22 @@
 // loop uses packed FP32x2 arithmetic (two columns per instruction) and one SFU
 // reciprocal per pair.
 //
+// Every row keeps two partial sums, one per half of each column tile (column pairs
+// [0, np/2) and [np/2, np) plus an odd last column), added together when the row
+// is finished. The halves fix each row's summation order whatever warp holds it,
+// and let the host spread the bulk work evenly over the SM's four sub-partitions:
+// a warp takes a whole row block or one half of one.
+//
+// With the tile ring, a minibatch's new positions are published into a slot of a
+// 4-slot ring as single 64-bit stores (release), each slot all-ones until written:
+// the control warp reads the previous minibatch's slots until every one is set and
+// thereby has the tile in one round trip (instead of a counter poll followed by a
+// copy). A CTA resets its share of the ring slot of step s-2 at the end of step s
+// (every CTA has read it by then: they all published step s-1 after reading it);
+// that slot is written again at step s+2 by CTAs that first read this CTA's step
+// s+1 publication, which follows the reset. The ring needs every CTA to publish in
+// every minibatch (minibatches of at least G rows); otherwise the counter is used.
+//
 // Positions are double-buffered by iteration parity: iteration t writes
 // buf[(t+1)&1] and reads not-yet-moved vertices from buf[t&1]. A CTA can lag
 // the others by at most one step, so nothing still to be read is overwritten.
@@ -116,14 +132,87 @@ struct EngineSmem {
         pos = tile + 2 * TQ * 16;                        // nloc float2: local positions
         rpl = pos + ((nloc * 8 + 15) / 16) * 16;         // nloc int: rowptr[i]
         rpe = rpl + ((nloc * 4 + 15) / 16) * 16;         // nloc int: rowptr[i+1]
-        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 x CR float2: critical sums
-        off = crep + ((2 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
+        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 steps x 2 halves x CR float2: critical sums
+        off = crep + ((4 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
         cid = off + ((3 * (CR + 1) * 4 + 15) / 16) * 16; // 3 x CAP int: staged column ids
         nbr = cid + 3 * CAP * 4;                         // 2 x CAP float2: staged positions
         ctl = nbr + 2 * CAP * 8;                         // control words
         total = ctl + 64;
     }
 };
+
+// ---- tile ring: one 64-bit slot per column, all-ones until the position is published
+constexpr unsigned long long kRingUnset = ~0ull;
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Publishes (x, y) as one 64-bit release store (x in the low word); a pair whose
+// bits equal the unset pattern (two all-ones NaNs) is published as canonical NaNs.
+__device__ __forceinline__ void ring_publish(unsigned long long* p, float x, float y) {
+    unsigned long long v = (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
+    if (v == kRingUnset) v = 0x7FFFFFFF7FFFFFFFull;
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ float4 ring_pair(unsigned long long a, unsigned long long b) {
+    return make_float4(__uint_as_float((unsigned)a), __uint_as_float((unsigned)b),
+                       __uint_as_float((unsigned)(a >> 32)), __uint_as_float((unsigned)(b >> 32)));
+}
+// The control warp copies the nc published columns of a ring slot into a paired
+// tile in shared memory, reading each slot until it is set (acquire loads, 8 per
+// lane in flight). Bounded: false (warp-uniform) when the wait gave up or another
+// CTA reported an error.
+__device__ __forceinline__ bool ring_tile(const unsigned long long* slot, int nc, float4* tile, int lane,
+                                          int* status) {
+    const int nq = (nc + 1) / 2;
+    unsigned long long t0 = 0;
+    for (int q0 = 0; q0 < nq; q0 += 128) {
+        unsigned long long va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int q = q0 + lane + 32 * u;
+            va[u] = q < nq ? ld_acquire_u64(slot + 2 * q) : 0ull;
+            vb[u] = (q < nq && 2 * q + 1 < nc) ? ld_acquire_u64(slot + 2 * q + 1) : 0ull;
+        }
+        for (unsigned spin = 0;; ++spin) {
+            bool pending = false;
+#pragma unroll
+            for (int u = 0; u < 4; u++) pending |= va[u] == kRingUnset || vb[u] == kRingUnset;
+            if (!__any_sync(0xffffffffu, pending)) break;
+            __nanosleep(32);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int q = q0 + lane + 32 * u;
+                if (va[u] == kRingUnset) va[u] = ld_acquire_u64(slot + 2 * q);
+                if (vb[u] == kRingUnset) vb[u] = ld_acquire_u64(slot + 2 * q + 1);
+            }
+            if ((spin & 255u) == 255u) {
+                int bad = 0;
+                if (lane == 0) {
+                    if (t0 == 0) t0 = global_ns();
+                    if (ld_volatile_i32(status) != 0) {
+                        bad = 1;
+                    } else if (global_ns() - t0 > kWaitLimitNs) {
+                        atomicCAS(status, 0, (int)BL_ETIMEOUT);
+                        bad = 1;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int q = q0 + lane + 32 * u;
+            if (q < nq) tile[q] = ring_pair(va[u], vb[u]);
+        }
+    }
+    __syncwarp();
+    return true;
+}
 
 // critical rows of batch k in CTA `rank`: local indices [lo, hi)
 __device__ __forceinline__ void crit_range(int k, int BS, int n, int rank, int G, int& lo,
@@ -194,6 +283,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     const bool kahan = prm.kahan != 0;
     float2* const buf0 = tk.pos;
     float2* const buf1 = tk.pos_alt;
+    unsigned long long* const ring = snapshot ? nullptr : tk.ring;
 
     // ---- bulk state: blocks of 32 consecutive local rows per warp (so a warp's rows
     //      share few minibatches and whole warps skip columns they do not need);
@@ -201,18 +291,22 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     //      control warp (hardware warp w runs on sub-partition w % 4) -------------------
     const int wslot = (wb + 1) % 4 == 0 ? (NW - NW / 4) + (wb + 1) / 4 - 1
                                          : wb - (wb + 1) / 4;
+    // this warp's piece: row block and halves of every column tile
+    const int pcode = is_ctl ? 0 : (tk.pieces_on ? tk.piece[wb] : (wslot | (3 << 16)));
+    const int blk = pcode & 0xFFFF, hmask = pcode >> 16;
     f32x2 XI[RPT], YI[RPT];
-    float sx[RPT], sy[RPT], cx[RPT], cy[RPT];
+    float sx[2][RPT], sy[2][RPT], cx[2][RPT], cy[2][RPT];   // per column half
     int bi[RPT], lrow[RPT];
 #pragma unroll
     for (int m = 0; m < RPT; m++) {
-        const int li = lane + 32 * (wslot + NW * m);
-        const bool v = !is_ctl && li < nloc;
+        const int li = lane + 32 * (blk + NW * m);
+        const bool v = !is_ctl && hmask != 0 && li < nloc;
         const int i = rank + G * li;
         const float2 p = v ? __ldcg(&buf0[i]) : make_float2(0.f, 0.f);
         XI[m] = pk2(p.x, p.x);
         YI[m] = pk2(p.y, p.y);
-        sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) sx[h][m] = sy[h][m] = cx[h][m] = cy[h][m] = 0.f;
         bi[m] = v ? i / BS : -1;
         lrow[m] = li;
     }
@@ -229,29 +323,35 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         int mlo, mhi;
         need_range<RPT>(need, mlo, mhi);
         if (mlo >= mhi) return;
-        f32x2 AX[RPT], AY[RPT];
+        const int np = nc >> 1, hp = np >> 1;   // column pairs; halves [0, hp) and [hp, np) + odd column
 #pragma unroll
-        for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
-        tile_pairs2<RPT>(tile, nc >> 1, mlo, mhi, XI, YI, AX, AY);
+        for (int h = 0; h < 2; h++) {
+            if (!(hmask & (1 << h))) continue;   // warp-uniform
+            const int q0 = h == 0 ? 0 : hp, q1 = h == 0 ? hp : np;
+            f32x2 AX[RPT], AY[RPT];
 #pragma unroll
-        for (int m = 0; m < RPT; m++) {
-            float a0, a1, b0, b1, xi, yi, dummy;
-            upk2(AX[m], a0, a1);
-            upk2(AY[m], b0, b1);
-            upk2(XI[m], xi, dummy);
-            upk2(YI[m], yi, dummy);
-            float ax = a0 + a1, ay = b0 + b1;
-            if (nc & 1) {
-                const float2 pc = tile_col(tile, nc - 1);
-                rep_pair(xi, yi, pc.x, pc.y, ax, ay);
-            }
-            if (need[m]) {
-                if (kahan) {   // compensated across the row's column tiles
-                    kahan_add(sx[m], cx[m], ax);
-                    kahan_add(sy[m], cy[m], ay);
-                } else {
-                    sx[m] += ax;
-                    sy[m] += ay;
+            for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
+            tile_pairs2<RPT>(tile + q0, q1 - q0, mlo, mhi, XI, YI, AX, AY);
+#pragma unroll
+            for (int m = 0; m < RPT; m++) {
+                float a0, a1, b0, b1, xi, yi, dummy;
+                upk2(AX[m], a0, a1);
+                upk2(AY[m], b0, b1);
+                upk2(XI[m], xi, dummy);
+                upk2(YI[m], yi, dummy);
+                float ax = a0 + a1, ay = b0 + b1;
+                if (h == 1 && (nc & 1)) {
+                    const float2 pc = tile_col(tile, nc - 1);
+                    rep_pair(xi, yi, pc.x, pc.y, ax, ay);
+                }
+                if (need[m]) {
+                    if (kahan) {   // compensated across the row's column tiles
+                        kahan_add(sx[h][m], cx[h][m], ax);
+                        kahan_add(sy[h][m], cy[h][m], ay);
+                    } else {
+                        sx[h][m] += ax;
+                        sy[h][m] += ay;
+                    }
                 }
             }
         }
@@ -307,7 +407,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         __syncthreads();
     }
 
-    // bulk: post the sums of the rows of batch kk into crep and restart them
+    // bulk: post the half sums of the rows of batch kk into crep (half h at
+    // crep[h * CR + row]) and restart them
     auto post_rows = [&](int kk, float2* crep) {
         int lo, hi;
         crit_range(kk, BS, n, rank, G, lo, hi);
@@ -315,8 +416,12 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         for (int m = 0; m < RPT; m++) {
             const int li = lrow[m];
             if (bi[m] == kk && li >= lo && li < hi) {
-                crep[li - lo] = make_float2(sx[m] - cx[m], sy[m] - cy[m]);
-                sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
+#pragma unroll
+                for (int h = 0; h < 2; h++)
+                    if (hmask & (1 << h)) {
+                        crep[h * CR + li - lo] = make_float2(sx[h][m] - cx[h][m], sy[h][m] - cy[h][m]);
+                        sx[h][m] = sy[h][m] = cx[h][m] = cy[h][m] = 0.f;
+                    }
             }
         }
     };
@@ -373,7 +478,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     // snapshot force). Returns this lane's energy contribution.
     auto ctl_critical = [&](int k, int kprev, int slot, int pslot, const float4* tile,
                             float stepf, const float2* bnew, const float2* bold,
-                            const float2* crep, float2* out) -> double {
+                            const float2* crep, float2* out, unsigned long long* rslot) -> double {
         int lo, hi;
         crit_range(k, BS, n, rank, G, lo, hi);
         const int* off = s_off + slot * (CR + 1);
@@ -460,7 +565,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 if (e1 - e0 > 32) {
                     ax = hax_g; ay = hay_g; qx = hqx_g; qy = hqy_g;
                 }
-                float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
+                // the two column halves of the bulk sums, in order
+                float sxr = crep[c].x + crep[CR + c].x, cxr = 0.f;
+                float syr = crep[c].y + crep[CR + c].y, cyr = 0.f;
                 if (kprev >= 0) {
                     if (kahan) {
                         kahan_add(sxr, cxr, rxs);
@@ -490,6 +597,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     }
                     out[i] = make_float2(nx, ny);
                     s_pos[li] = make_float2(nx, ny);
+                    if (rslot != nullptr) ring_publish(rslot + (i - k * BS), nx, ny);
                     e += (double)fmaf(fx, fx, fy * fy);   // |ct|^2 in FP32, summed in FP64
                 }
             }
@@ -510,7 +618,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 __syncwarp();
             }
             __syncthreads();
-            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out);
+            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out, nullptr);
             __syncthreads();
         }
         return;
@@ -543,7 +651,19 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             const int kprev = (k + B - 1) % B;   // step 0: the last batch at the start positions
             float4* tile = s_tile + (size_t)(s & 1) * TQ;
             if (lane == 0) trace_mark(tk, rank, s, 0);
-            if (s > 0) {
+            if (s > 0 && ring != nullptr) {
+                // batch kprev from its ring slot (published at step s-1): waiting for
+                // it and copying the tile are one round trip
+                const int nc = min(BS, n - kprev * BS);
+                const bool ok = ring_tile(ring + (size_t)((s - 1) % kRingSlots) * BS, nc, tile, lane, prm.status);
+                if (lane == 0) trace_mark(tk, rank, s, 1);
+                if (!ok) {
+                    s_ctl[0] = 1;                 // tell the bulk warps to leave
+                    bar_sync_n(kBarDone, T);      // their step s-1 is over
+                    bar_arrive_n(kBarTile, T);
+                    return;
+                }
+            } else if (s > 0) {
                 // wait until every CTA has published batch kprev (bounded)
                 int ok = 1;
                 if (lane == 0) {
@@ -572,7 +692,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     return;
                 }
             }
-            {
+            if (s == 0 || ring == nullptr) {
                 // the buffer batch kprev was written to at step s-1 (step 0: the
                 // launch's start positions)
                 const float2* bprev = s == 0 ? buf0 : ((k == 0) ? bold : bnew);
@@ -603,11 +723,22 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (lane == 0) trace_mark(tk, rank, s, 3);
             bar_arrive_n(kBarTile, T);            // bulk may start step s
             const double e = ctl_critical(k, kprev, s % 3, s & 1, tile, (float)step, bnew, bold,
-                                          s_crep + (size_t)(s & 1) * CR, bnew);
+                                          s_crep + (size_t)(s & 1) * 2 * CR, bnew,
+                                          ring != nullptr ? ring + (size_t)(s % kRingSlots) * BS : nullptr);
             if (lane == 0) trace_mark(tk, rank, s, 4);
             e_iter += e;
             __syncwarp();
-            if (lane == 0) {
+            if (ring != nullptr) {
+                // this CTA's share of the ring slot of step s-2 back to unset: every CTA
+                // has read it (they all published step s-1 after reading it), and it is
+                // written again at step s+2, after this CTA's step s+1 publication
+                if (s >= 2) {
+                    unsigned long long* old = ring + (size_t)((s - 2) % kRingSlots) * BS;
+                    for (int q = rank + G * lane; q < BS; q += G * 32) st_relaxed_u64(old + q, kRingUnset);
+                }
+                __syncwarp();
+                if (lane == 0) trace_mark(tk, rank, s, 6);
+            } else if (lane == 0) {
                 red_release_add_u32(prm.bar, 1u);   // this CTA's part of batch k is out
                 trace_mark(tk, rank, s, 6);
             }
@@ -651,7 +782,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 need[m] = bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
             if (tb == 0) trace_mark(tk, rank, s, 10);
             add_tile(tile, kpn, need);
-            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * CR);
+            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * 2 * CR);
             if (is_stager) cp_async_wait_all();   // staged data lands before "done"
             if (tb == 0) trace_mark(tk, rank, s, 8);
             bar_arrive_n(kBarDone, T);
@@ -698,6 +829,8 @@ static bl_status launch_grid_t(const ExactPlan& pl, const ExactTask& tk, const E
     if (pl.G > occ * device_sm_count())
         return set_error(BL_EINVAL, "exact engine: grid exceeds co-resident CTAs");
     ExactTask t = tk;
+    t.pieces_on = pl.pieces_on;
+    for (int w = 0; w < 16; w++) t.piece[w] = pl.piece[w];
     ExactParams p = prm;
     void* args[] = {&t, &p};
     BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(pl.G), dim3(T), args, smem, st));
@@ -728,6 +861,39 @@ static bl_status dispatch_rpt(const ExactPlan& pl, const ExactTask& tk, const Ex
 // bulk rounded up to whole warps (256, 320, 384, 448 or 512 threads) so that few
 // lanes idle in the pair loop; up to 2048 rows 512 threads x 2..4 rows, beyond
 // that 256 threads x 6..8 rows.
+// Bulk pieces for one row per thread: the nb row blocks of 32 rows are 2 nb half
+// units (a block over one half of every column tile); each sub-partition gets an
+// equal share (the one the control warp shares gets the smaller one when they
+// cannot be equal), as whole blocks plus at most one half, and a split block's two
+// halves go to two sub-partitions. Bulk warp w runs on sub-partition (w + 1) % 4;
+// the half pieces go to each sub-partition's last warps (on sub-partition 0 that
+// is the warp that also stages neighbours). Off (0) when it does not fit.
+static int plan_pieces(int nloc, int T, int* piece) {
+    const int NW = T / 32, per = NW / 4;
+    const int nb = (nloc + 31) / 32;
+    if (NW % 4 != 0 || nb > NW || nb == 0) return 0;
+    int h[4];
+    const int H = 2 * nb;
+    for (int j = 0; j < 4; j++) h[j] = H / 4;
+    for (int j = 1, r = H % 4; r > 0; j = (j % 3) + 1, r--) h[j]++;   // extra halves to 1, 2, 3
+    std::vector<int> warps[4];
+    for (int w = 0; w < NW; w++) warps[(w + 1) % 4].push_back(w);
+    for (int j = 0; j < 4; j++)
+        if (h[j] / 2 + h[j] % 2 > per) return 0;
+    for (int w = 0; w < NW; w++) piece[w] = 0;   // idle
+    int blk = 0;
+    const int order[4] = {1, 2, 3, 0};
+    for (int j : order)
+        for (int f = 0; f < h[j] / 2; f++) piece[warps[j][f]] = blk++ | (3 << 16);
+    int half = 0;   // the rest in halves: first half, then second, of each block in turn
+    for (int j : order)
+        if (h[j] % 2) {
+            piece[warps[j][h[j] / 2]] = (blk + half / 2) | ((half % 2 == 0 ? 1 : 2) << 16);
+            half++;
+        }
+    return (blk + half / 2 == nb && half % 2 == 0) ? 1 : 0;
+}
+
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out) {
     if (n <= 0 || BS <= 0) return set_error(BL_EINVAL, "exact engine: empty problem");
     const int sms = device_sm_count();
@@ -769,6 +935,12 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
     out->G = G;
     out->T = T;
     out->rpt = chosen;
+    out->pieces_on = 0;
+    for (int w = 0; w < 16; w++) out->piece[w] = 0;
+    {
+        const char* e = std::getenv("BL_EXACT_PIECES");   // 0: every warp a whole row block
+        if (chosen == 1 && !(e && e[0] == '0')) out->pieces_on = plan_pieces(nloc, T, out->piece);
+    }
     out->crit_cap = div_up(std::min(BS, n), G) + 1;
     out->nbr_cap = 2048;
     while (EngineSmem(BS, nloc, out->crit_cap, out->nbr_cap, T / 32).total > 200 * 1024 &&

@@ -116,6 +116,7 @@ struct bl_layout {
     bl::Allocator alloc;
     int trace_steps = 0;                // phase trace of the next run (0 = off)
     bl::DevBuf trace;                   // uint64 timestamps
+    bl::DevBuf ring;                    // exact engine's tile ring (kRingSlots x batch)
     int64_t trace_count = 0;            // entries written by the last traced run
     int phase_timing = 0;               // Barnes-Hut phase events on (bl_set_phase_timing)
     double phase_ms[9] = {};            // phase times of the last timed BH run (bl_get_phase_times)
@@ -149,7 +150,15 @@ struct ExactTask {
     int nbr_cap;         // neighbour positions staged in shared memory
     unsigned long long* trace;   // optional phase timestamps [G][trace_steps][kTraceSlots]
     int trace_steps;
+    // bulk work pieces (rows per thread 1): piece[w] = row block | halves << 16 of bulk
+    // warp w, halves bit 0 = the first half of every column tile, bit 1 = the second
+    int pieces_on;
+    int piece[16];
+    // tile ring (null: the step counter instead): kRingSlots x BS 64-bit slots, one
+    // published position each, all-ones until published
+    unsigned long long* ring;
 };
+constexpr int kRingSlots = 4;
 
 struct ExactParams {
     float invK;          // 1/K
@@ -166,6 +175,8 @@ struct ExactParams {
 struct ExactPlan {
     int G, T, rpt;
     int crit_cap, nbr_cap;   // see ExactTask
+    int pieces_on;           // see ExactTask
+    int piece[16];
 };
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out);
 

@@ -187,6 +187,15 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     if (!snapshot) {
         BL_TRY(L->epart.ensure(L->alloc, (size_t)iters * plan.G * sizeof(double)));
         tk.e_iter = L->epart.as<double>();
+        // the tile ring, when every minibatch has a row on every CTA (BL_EXACT_RING=0: the counter)
+        const int last = n - (tk.B - 1) * BS;
+        const char* e = std::getenv("BL_EXACT_RING");
+        if (BS >= plan.G && last >= plan.G && !(e && e[0] == '0')) {
+            const size_t rb = (size_t)kRingSlots * BS * sizeof(unsigned long long);
+            BL_TRY(L->ring.ensure(L->alloc, rb));
+            BL_CUDA_TRY(cudaMemsetAsync(L->ring.p, 0xFF, rb, st));
+            tk.ring = L->ring.as<unsigned long long>();
+        }
     }
     ExactParams prm{};
     prm.invK = 1.0f / L->prm.K;
@@ -220,6 +229,7 @@ void layout_destroy(bl_layout* L) {
     L->status.release();
     L->scratch.release();
     L->trace.release();
+    L->ring.release();
     delete L;
 }
 
