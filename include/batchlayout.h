@@ -325,6 +325,12 @@ bl_status bl_layout_run_noalloc(int32_t n, const int32_t *d_rowptr, const int32_
  * returns BL_ETIMEOUT with the context still usable. Synchronises. */
 bl_status bl_debug_barrier_timeout(int32_t limit_ms);
 
+/* Test hook (the paper has no counterpart): evaluates on the device the
+ * reciprocal the exact engine's control warp takes on the FMA pipe (Newton-Raphson,
+ * used when BL_EXACT_CTL_NR=1) for n host floats x > 0 (1 <= n <= 2^26);
+ * y receives n floats. Synchronises. */
+bl_status bl_debug_rcp(const float *x, float *y, int64_t n);
+
 /* ---- parity hooks ------------------------------------------------------------ */
 
 /* One-snapshot forces ct_i (FP32, 2 floats per vertex) for i in [lo, hi) from
@@ -356,9 +362,9 @@ bl_status bl_debug_bh_counts(bl_layout *L, float theta, int32_t *far, int32_t *n
  * minibatch steps of the next exact-mode bl_layout_run (0 turns it off). Per
  * CTA and step, 12 slots: control warp {0 step start, 1 previous batch
  * published by all CTAs, 2 column tile in shared memory, 3 bulk warps done with
- * the previous step, 4 critical rows moved, 6 arrival posted}; bulk warps {7
- * step start, 5 moved rows picked up, 10 neighbours staged, 8 step done};
- * slots 9 and 11 unused (0). In BH mode (any max_steps > 0) the last
+ * the previous step, 9 first critical rows' column pass summed, 11 their CSR
+ * terms summed, 4 critical rows moved, 6 arrival posted}; bulk warps {7 step
+ * start, 5 moved rows picked up, 10 neighbours staged, 8 step done}. In BH mode (any max_steps > 0) the last
  * iteration's sweep is traced instead: the start time of each of its dependency
  * levels, then its end. */
 bl_status bl_set_trace(bl_layout *L, int32_t max_steps);

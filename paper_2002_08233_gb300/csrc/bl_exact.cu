@@ -28,21 +28,28 @@
 // loop uses packed FP32x2 arithmetic (two columns per instruction) and one SFU
 // reciprocal per pair.
 //
-// Every row keeps two partial sums, one per half of each column tile (column pairs
-// [0, np/2) and [np/2, np) plus an odd last column), added together when the row
-// is finished. The halves fix each row's summation order whatever warp holds it,
-// and let the host spread the bulk work evenly over the SM's four sub-partitions:
-// a warp takes a whole row block or one half of one.
+// With bulk pieces on (rows per thread 1, BL_EXACT_PIECES=1), every row keeps two
+// partial sums, one per half of each column tile (column pairs [0, np/2) and
+// [np/2, np) plus an odd last column), added together when the row is finished;
+// the host then spreads the bulk work evenly over the SM's four sub-partitions,
+// a warp taking a whole row block or one half of one. Otherwise a row has one
+// sum per tile. Either way a row's summation order does not depend on which
+// warp holds it.
 //
 // With the tile ring, a minibatch's new positions are published into a slot of a
-// 4-slot ring as single 64-bit stores (release), each slot all-ones until written:
-// the control warp reads the previous minibatch's slots until every one is set and
+// 4-slot ring as single 64-bit stores, each slot all-ones until written: the
+// control warp reads the previous minibatch's slots until every one is set and
 // thereby has the tile in one round trip (instead of a counter poll followed by a
-// copy). A CTA resets its share of the ring slot of step s-2 at the end of step s
-// (every CTA has read it by then: they all published step s-1 after reading it);
-// that slot is written again at step s+2 by CTAs that first read this CTA's step
-// s+1 publication, which follows the reset. The ring needs every CTA to publish in
-// every minibatch (minibatches of at least G rows); otherwise the counter is used.
+// copy), then takes an acquire-release fence. That fence is also what orders this
+// CTA's earlier writes (its positions, its slot resets) before its next
+// publication, so the publications themselves are relaxed; in exchange the
+// critical rows take the two most recent minibatches' positions from the current
+// and the previous tile in shared memory, never from global memory. A CTA resets
+// its share of the ring slot of step s-2 at the end of step s (every CTA has read
+// it by then: they all published step s-1 after reading it); that slot is written
+// again at step s+2 by CTAs that first read this CTA's step s+1 publication, which
+// follows the reset and a fence. The ring needs every CTA to publish in every
+// minibatch (minibatches of at least G rows); otherwise the counter is used.
 //
 // Positions are double-buffered by iteration parity: iteration t writes
 // buf[(t+1)&1] and reads not-yet-moved vertices from buf[t&1]. A CTA can lag
@@ -143,29 +150,34 @@ struct EngineSmem {
 
 // ---- tile ring: one 64-bit slot per column, all-ones until the position is published
 constexpr unsigned long long kRingUnset = ~0ull;
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-// Publishes (x, y) as one 64-bit release store (x in the low word); a pair whose
-// bits equal the unset pattern (two all-ones NaNs) is published as canonical NaNs.
+// Publishes (x, y) as one 64-bit store (x in the low word); a pair whose bits
+// equal the unset pattern (two all-ones NaNs) is published as canonical NaNs. The
+// store is relaxed: the acquire-release fence the control warp takes after each
+// ring read orders everything the CTA wrote before it (positions, slot resets)
+// before the CTA's next publication.
 __device__ __forceinline__ void ring_publish(unsigned long long* p, float x, float y) {
     unsigned long long v = (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
     if (v == kRingUnset) v = 0x7FFFFFFF7FFFFFFFull;
-    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    st_relaxed_u64(p, v);
 }
 __device__ __forceinline__ float4 ring_pair(unsigned long long a, unsigned long long b) {
     return make_float4(__uint_as_float((unsigned)a), __uint_as_float((unsigned)b),
                        __uint_as_float((unsigned)(a >> 32)), __uint_as_float((unsigned)(b >> 32)));
 }
 // The control warp copies the nc published columns of a ring slot into a paired
-// tile in shared memory, reading each slot until it is set (acquire loads, 8 per
-// lane in flight). Bounded: false (warp-uniform) when the wait gave up or another
-// CTA reported an error.
+// tile in shared memory, reading each slot until it is set (relaxed loads, 8 per
+// lane in flight; acquire loads would be issued one after another), then takes
+// one acquire fence so that what the publishers wrote before their release stores
+// is visible to this CTA. Bounded: false (warp-uniform) when the wait gave up or
+// another CTA reported an error.
 __device__ __forceinline__ bool ring_tile(const unsigned long long* slot, int nc, float4* tile, int lane,
                                           int* status) {
     const int nq = (nc + 1) / 2;
@@ -175,8 +187,8 @@ __device__ __forceinline__ bool ring_tile(const unsigned long long* slot, int nc
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const int q = q0 + lane + 32 * u;
-            va[u] = q < nq ? ld_acquire_u64(slot + 2 * q) : 0ull;
-            vb[u] = (q < nq && 2 * q + 1 < nc) ? ld_acquire_u64(slot + 2 * q + 1) : 0ull;
+            va[u] = q < nq ? ld_relaxed_u64(slot + 2 * q) : 0ull;
+            vb[u] = (q < nq && 2 * q + 1 < nc) ? ld_relaxed_u64(slot + 2 * q + 1) : 0ull;
         }
         for (unsigned spin = 0;; ++spin) {
             bool pending = false;
@@ -187,8 +199,8 @@ __device__ __forceinline__ bool ring_tile(const unsigned long long* slot, int nc
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int q = q0 + lane + 32 * u;
-                if (va[u] == kRingUnset) va[u] = ld_acquire_u64(slot + 2 * q);
-                if (vb[u] == kRingUnset) vb[u] = ld_acquire_u64(slot + 2 * q + 1);
+                if (va[u] == kRingUnset) va[u] = ld_relaxed_u64(slot + 2 * q);
+                if (vb[u] == kRingUnset) vb[u] = ld_relaxed_u64(slot + 2 * q + 1);
             }
             if ((spin & 255u) == 255u) {
                 int bad = 0;
@@ -210,6 +222,7 @@ __device__ __forceinline__ bool ring_tile(const unsigned long long* slot, int nc
             if (q < nq) tile[q] = ring_pair(va[u], vb[u]);
         }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     __syncwarp();
     return true;
 }
@@ -323,10 +336,12 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         int mlo, mhi;
         need_range<RPT>(need, mlo, mhi);
         if (mlo >= mhi) return;
-        const int np = nc >> 1, hp = np >> 1;   // column pairs; halves [0, hp) and [hp, np) + odd column
+        // column pairs; with pieces the halves [0, hp) and [hp, np) + odd column,
+        // without them one pass over the whole tile into the first accumulator
+        const int np = nc >> 1, hp = tk.pieces_on ? (np >> 1) : np;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            if (!(hmask & (1 << h))) continue;   // warp-uniform
+            if (!(hmask & (1 << h)) || (h == 1 && !tk.pieces_on)) continue;   // warp-uniform
             const int q0 = h == 0 ? 0 : hp, q1 = h == 0 ? hp : np;
             f32x2 AX[RPT], AY[RPT];
 #pragma unroll
@@ -340,7 +355,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 upk2(XI[m], xi, dummy);
                 upk2(YI[m], yi, dummy);
                 float ax = a0 + a1, ay = b0 + b1;
-                if (h == 1 && (nc & 1)) {
+                if ((h == 1 || !tk.pieces_on) && (nc & 1)) {
                     const float2 pc = tile_col(tile, nc - 1);
                     rep_pair(xi, yi, pc.x, pc.y, ax, ay);
                 }
@@ -453,8 +468,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     // positions of those neighbours (ids in `slot`, landed) into position slot
     // `pslot`, as the step of batch kk reads them (bnew/bold: that step's buffers):
     // batch(j) < kk moved in this iteration (bnew), batch(j) >= kk not yet (bold);
-    // batch kprev comes from the column tile instead (kprev < 0: no tile)
-    auto stage_pos = [&](int kk, int kprev, int slot, int pslot, const float2* bnew,
+    // batches kprev and kprev2 come from that step's column tile and the one before
+    // it instead (< 0: no such tile)
+    auto stage_pos = [&](int kk, int kprev, int kprev2, int slot, int pslot, const float2* bnew,
                          const float2* bold) {
         int lo, hi;
         crit_range(kk, BS, n, rank, G, lo, hi);
@@ -465,7 +481,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         for (int f = lane; f < tot; f += 32) {
             const int j = cid[f];
             const int bj = j / BS;
-            if (kprev >= 0 && bj == kprev) continue;
+            if ((kprev >= 0 && bj == kprev) || (kprev2 >= 0 && bj == kprev2)) continue;
             cp_async8(&nbr[f], bj < kk ? bnew + j : bold + j);
         }
         cp_async_commit();
@@ -476,8 +492,10 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     // 3-level butterfly inside each 8-lane group. CSR: one lane per row (rows with
     // more than 32 edges: the whole warp). Lane r then moves row r (or records the
     // snapshot force). Returns this lane's energy contribution.
-    auto ctl_critical = [&](int k, int kprev, int slot, int pslot, const float4* tile,
-                            float stepf, const float2* bnew, const float2* bold,
+    int cur_s = 0;   // step being traced (control warp)
+    // kprev2 / ptile: the batch of the previous step's tile and that tile (kprev2 < 0: none)
+    auto ctl_critical = [&](int k, int kprev, int kprev2, int slot, int pslot, const float4* tile,
+                            const float4* ptile, float stepf, const float2* bnew, const float2* bold,
                             const float2* crep, float2* out, unsigned long long* rslot) -> double {
         int lo, hi;
         crit_range(k, BS, n, rank, G, lo, hi);
@@ -486,11 +504,15 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         const float2* nbr = s_nbr + (size_t)pslot * CAP;
         const int kplo = kprev >= 0 ? kprev * BS : 0;
         const int kpn = kprev >= 0 ? min(BS, n - kplo) : 0;
+        const int kplo2 = kprev2 >= 0 ? kprev2 * BS : 0;
+        const int kpn2 = kprev2 >= 0 && kprev2 != kprev ? min(BS, n - kplo2) : 0;
         auto nbr_pos = [&](int c, int ee, int e0) -> float2 {
             const int f = off[c] + (ee - e0);
             const int j = f < CAP ? cid[f] : __ldg(&tk.colids[ee]);
             const unsigned o = (unsigned)(j - kplo);
             if (o < (unsigned)kpn) return tile_col(tile, (int)o);
+            const unsigned o2 = (unsigned)(j - kplo2);
+            if (o2 < (unsigned)kpn2) return tile_col(ptile, (int)o2);
             if (f < CAP) return nbr[f];
             return __ldcg(j < k * BS ? bnew + j : bold + j);
         };
@@ -505,16 +527,25 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             float rx = 0.f, ry = 0.f;
             if (g < nr) {   // unrolled: the loads and reciprocals of 8 columns overlap
                 const float2 me = s_pos[lo + c0 + g];
+                if (prm.ctl_nr) {   // off the SFU, which the bulk warps keep busy (uniform)
 #pragma unroll 8
-                for (int q = gl; q < kpn; q += W) {
-                    const float2 pc = tile_col(tile, q);
-                    rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
+                    for (int q = gl; q < kpn; q += W) {
+                        const float2 pc = tile_col(tile, q);
+                        rep_pair_nr(me.x, me.y, pc.x, pc.y, rx, ry);
+                    }
+                } else {
+#pragma unroll 8
+                    for (int q = gl; q < kpn; q += W) {
+                        const float2 pc = tile_col(tile, q);
+                        rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
+                    }
                 }
             }
             for (int o = W >> 1; o > 0; o >>= 1) {
                 rx += __shfl_xor_sync(0xffffffffu, rx, o);
                 ry += __shfl_xor_sync(0xffffffffu, ry, o);
             }
+            if (lane == 0 && c0 == 0 && !snapshot) trace_mark(tk, rank, cur_s, 9);
             // hub rows: whole-warp CSR sums
             float hax = 0.f, hay = 0.f, hqx = 0.f, hqy = 0.f;
             for (int r = 0; r < nr; r++) {
@@ -550,6 +581,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 qx += __shfl_xor_sync(0xffffffffu, qx, o);
                 qy += __shfl_xor_sync(0xffffffffu, qy, o);
             }
+            if (lane == 0 && c0 == 0 && !snapshot) trace_mark(tk, rank, cur_s, 11);
             // the first lane of group g finishes row c0 + g (hub sums sit in lane g)
             const float hax_g = __shfl_sync(0xffffffffu, hax, g & 31);
             const float hay_g = __shfl_sync(0xffffffffu, hay, g & 31);
@@ -613,12 +645,12 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 stage_ids(k, 0);
                 cp_async_wait_all();
                 __syncwarp();
-                stage_pos(k, -1, 0, 0, buf0, buf0);
+                stage_pos(k, -1, -1, 0, 0, buf0, buf0);
                 cp_async_wait_all();
                 __syncwarp();
             }
             __syncthreads();
-            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out, nullptr);
+            if (is_ctl) ctl_critical(k, -1, -1, 0, 0, s_tile, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out, nullptr);
             __syncthreads();
         }
         return;
@@ -633,7 +665,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         if (S > 1) stage_ids(1 % B, 1);
         cp_async_wait_all();
         __syncwarp();
-        stage_pos(0, -1, 0, 0, buf1, buf0);
+        stage_pos(0, -1, -1, 0, 0, buf1, buf0);
         cp_async_wait_all();
         __syncwarp();
     }
@@ -650,6 +682,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             float2* bnew = (it & 1) ? buf0 : buf1;
             const int kprev = (k + B - 1) % B;   // step 0: the last batch at the start positions
             float4* tile = s_tile + (size_t)(s & 1) * TQ;
+            cur_s = s;
             if (lane == 0) trace_mark(tk, rank, s, 0);
             if (s > 0 && ring != nullptr) {
                 // batch kprev from its ring slot (published at step s-1): waiting for
@@ -722,7 +755,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (s > 0) bar_sync_n(kBarDone, T);   // bulk finished step s-1
             if (lane == 0) trace_mark(tk, rank, s, 3);
             bar_arrive_n(kBarTile, T);            // bulk may start step s
-            const double e = ctl_critical(k, kprev, s % 3, s & 1, tile, (float)step, bnew, bold,
+            const int kprev2 = s > 0 ? ((k - 2) % B + B) % B : -1;   // batch of step s-1's tile
+            const double e = ctl_critical(k, kprev, kprev2, s % 3, s & 1, tile,
+                                          s_tile + (size_t)((s + 1) & 1) * TQ, (float)step, bnew, bold,
                                           s_crep + (size_t)(s & 1) * 2 * CR, bnew,
                                           ring != nullptr ? ring + (size_t)(s % kRingSlots) * BS : nullptr);
             if (lane == 0) trace_mark(tk, rank, s, 4);
@@ -771,7 +806,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (is_stager && s + 1 < S) {   // neighbours of step s+1, ids of step s+2
                 const int kn = (k + 1) % B;
                 const int itn = kn == 0 ? it + 1 : it;
-                stage_pos(kn, k, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1,
+                stage_pos(kn, k, (k + B - 1) % B, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1,
                           (itn & 1) ? buf1 : buf0);
                 if (s + 2 < S) stage_ids((k + 2) % B, (s + 2) % 3);
             }
@@ -894,6 +929,11 @@ static int plan_pieces(int nloc, int T, int* piece) {
     return (blk + half / 2 == nb && half % 2 == 0) ? 1 : 0;
 }
 
+int exact_ctl_nr() {
+    const char* e = std::getenv("BL_EXACT_CTL_NR");
+    return (e && e[0] == '1') ? 1 : 0;
+}
+
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out) {
     if (n <= 0 || BS <= 0) return set_error(BL_EINVAL, "exact engine: empty problem");
     const int sms = device_sm_count();
@@ -938,8 +978,8 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
     out->pieces_on = 0;
     for (int w = 0; w < 16; w++) out->piece[w] = 0;
     {
-        const char* e = std::getenv("BL_EXACT_PIECES");   // 0: every warp a whole row block
-        if (chosen == 1 && !(e && e[0] == '0')) out->pieces_on = plan_pieces(nloc, T, out->piece);
+        const char* e = std::getenv("BL_EXACT_PIECES");   // 1: balanced pieces (column halves)
+        if (chosen == 1 && e && e[0] == '1') out->pieces_on = plan_pieces(nloc, T, out->piece);
     }
     out->crit_cap = div_up(std::min(BS, n), G) + 1;
     out->nbr_cap = 2048;

@@ -203,6 +203,7 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     prm.repulse_neighbors = L->prm.repulse_neighbors;
     prm.am = model_exponent(L->prm.energy_model);
     prm.kahan = kahan_on(L->prm.kahan, n) ? 1 : 0;
+    prm.ctl_nr = exact_ctl_nr();
     prm.status = static_cast<int*>(L->status.p);
     prm.bar = layout_barrier_word(L);
     BL_TRY(layout_reset_sync_words(L, st));
