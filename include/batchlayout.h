@@ -325,12 +325,6 @@ bl_status bl_layout_run_noalloc(int32_t n, const int32_t *d_rowptr, const int32_
  * returns BL_ETIMEOUT with the context still usable. Synchronises. */
 bl_status bl_debug_barrier_timeout(int32_t limit_ms);
 
-/* Test hook (the paper has no counterpart): evaluates on the device the
- * reciprocal the exact engine's control warp takes on the FMA pipe (Newton-Raphson,
- * used when BL_EXACT_CTL_NR=1) for n host floats x > 0 (1 <= n <= 2^26);
- * y receives n floats. Synchronises. */
-bl_status bl_debug_rcp(const float *x, float *y, int64_t n);
-
 /* ---- parity hooks ------------------------------------------------------------ */
 
 /* One-snapshot forces ct_i (FP32, 2 floats per vertex) for i in [lo, hi) from

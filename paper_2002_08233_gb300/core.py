@@ -93,7 +93,6 @@ def _declare(lib):
         "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
         "bl_layout_run_batch": [P, i32, i32, i32],
         "bl_debug_barrier_timeout": [i32],
-        "bl_debug_rcp": [P, P, i64],
         "bl_layout_init_greedy": [P, i64, u64, P, PP],
         "bl_layout_run_until": [P, i32, i32, ctypes.c_int, f32, f64, P, P],
     }

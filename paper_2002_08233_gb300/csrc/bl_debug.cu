@@ -18,11 +18,6 @@ __global__ void barrier_timeout_kernel(unsigned* ctr, int* status, unsigned long
     gb.sync();
 }
 
-__global__ void rcp_nr_kernel(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = rcp_nr(x[i]);
-}
-
 }  // namespace
 }  // namespace bl
 
@@ -49,27 +44,4 @@ extern "C" bl_status bl_debug_barrier_timeout(int32_t limit_ms) {
     if (s != BL_OK) return s;
     if (h != 0) return set_error((bl_status)h, "a bounded device-side wait timed out");
     return BL_OK;
-}
-
-// The FMA-pipe reciprocal the exact engine's control warp may use, evaluated on
-// the device for n host inputs (tests compare it with 1/x).
-extern "C" bl_status bl_debug_rcp(const float* x, float* y, int64_t n) {
-    if (!x || !y || n < 1 || n > (1ll << 26)) return set_error(BL_EINVAL, "bl_debug_rcp: bad argument");
-    cudaStream_t st = current_stream();
-    const Allocator al = current_allocator();
-    DevBuf buf;
-    BL_TRY(buf.ensure(al, (size_t)n * 2 * sizeof(float)));
-    float* dx = buf.as<float>();
-    float* dy = dx + n;
-    cudaError_t e = cudaMemcpyAsync(dx, x, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
-        rcp_nr_kernel<<<div_up(n, 256), 256, 0, st>>>(dx, dy, n);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(y, dy, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    bl_status s = e == cudaSuccess ? BL_OK : cuda_error(e, "bl_debug_rcp");
-    if (e != cudaSuccess) cudaStreamSynchronize(st);
-    buf.release();
-    return s;
 }

@@ -28,29 +28,6 @@
 // loop uses packed FP32x2 arithmetic (two columns per instruction) and one SFU
 // reciprocal per pair.
 //
-// With bulk pieces on (rows per thread 1, BL_EXACT_PIECES=1), every row keeps two
-// partial sums, one per half of each column tile (column pairs [0, np/2) and
-// [np/2, np) plus an odd last column), added together when the row is finished;
-// the host then spreads the bulk work evenly over the SM's four sub-partitions,
-// a warp taking a whole row block or one half of one. Otherwise a row has one
-// sum per tile. Either way a row's summation order does not depend on which
-// warp holds it.
-//
-// With the tile ring, a minibatch's new positions are published into a slot of a
-// 4-slot ring as single 64-bit stores, each slot all-ones until written: the
-// control warp reads the previous minibatch's slots until every one is set and
-// thereby has the tile in one round trip (instead of a counter poll followed by a
-// copy), then takes an acquire-release fence. That fence is also what orders this
-// CTA's earlier writes (its positions, its slot resets) before its next
-// publication, so the publications themselves are relaxed; in exchange the
-// critical rows take the two most recent minibatches' positions from the current
-// and the previous tile in shared memory, never from global memory. A CTA resets
-// its share of the ring slot of step s-2 at the end of step s (every CTA has read
-// it by then: they all published step s-1 after reading it); that slot is written
-// again at step s+2 by CTAs that first read this CTA's step s+1 publication, which
-// follows the reset and a fence. The ring needs every CTA to publish in every
-// minibatch (minibatches of at least G rows); otherwise the counter is used.
-//
 // Positions are double-buffered by iteration parity: iteration t writes
 // buf[(t+1)&1] and reads not-yet-moved vertices from buf[t&1]. A CTA can lag
 // the others by at most one step, so nothing still to be read is overwritten.
@@ -139,93 +116,14 @@ struct EngineSmem {
         pos = tile + 2 * TQ * 16;                        // nloc float2: local positions
         rpl = pos + ((nloc * 8 + 15) / 16) * 16;         // nloc int: rowptr[i]
         rpe = rpl + ((nloc * 4 + 15) / 16) * 16;         // nloc int: rowptr[i+1]
-        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 steps x 2 halves x CR float2: critical sums
-        off = crep + ((4 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
+        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 x CR float2: critical sums
+        off = crep + ((2 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
         cid = off + ((3 * (CR + 1) * 4 + 15) / 16) * 16; // 3 x CAP int: staged column ids
         nbr = cid + 3 * CAP * 4;                         // 2 x CAP float2: staged positions
         ctl = nbr + 2 * CAP * 8;                         // control words
         total = ctl + 64;
     }
 };
-
-// ---- tile ring: one 64-bit slot per column, all-ones until the position is published
-constexpr unsigned long long kRingUnset = ~0ull;
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-// Publishes (x, y) as one 64-bit store (x in the low word); a pair whose bits
-// equal the unset pattern (two all-ones NaNs) is published as canonical NaNs. The
-// store is relaxed: the acquire-release fence the control warp takes after each
-// ring read orders everything the CTA wrote before it (positions, slot resets)
-// before the CTA's next publication.
-__device__ __forceinline__ void ring_publish(unsigned long long* p, float x, float y) {
-    unsigned long long v = (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
-    if (v == kRingUnset) v = 0x7FFFFFFF7FFFFFFFull;
-    st_relaxed_u64(p, v);
-}
-__device__ __forceinline__ float4 ring_pair(unsigned long long a, unsigned long long b) {
-    return make_float4(__uint_as_float((unsigned)a), __uint_as_float((unsigned)b),
-                       __uint_as_float((unsigned)(a >> 32)), __uint_as_float((unsigned)(b >> 32)));
-}
-// The control warp copies the nc published columns of a ring slot into a paired
-// tile in shared memory, reading each slot until it is set (relaxed loads, 8 per
-// lane in flight; acquire loads would be issued one after another), then takes
-// one acquire fence so that what the publishers wrote before their release stores
-// is visible to this CTA. Bounded: false (warp-uniform) when the wait gave up or
-// another CTA reported an error.
-__device__ __forceinline__ bool ring_tile(const unsigned long long* slot, int nc, float4* tile, int lane,
-                                          int* status) {
-    const int nq = (nc + 1) / 2;
-    unsigned long long t0 = 0;
-    for (int q0 = 0; q0 < nq; q0 += 128) {
-        unsigned long long va[4], vb[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int q = q0 + lane + 32 * u;
-            va[u] = q < nq ? ld_relaxed_u64(slot + 2 * q) : 0ull;
-            vb[u] = (q < nq && 2 * q + 1 < nc) ? ld_relaxed_u64(slot + 2 * q + 1) : 0ull;
-        }
-        for (unsigned spin = 0;; ++spin) {
-            bool pending = false;
-#pragma unroll
-            for (int u = 0; u < 4; u++) pending |= va[u] == kRingUnset || vb[u] == kRingUnset;
-            if (!__any_sync(0xffffffffu, pending)) break;
-            __nanosleep(32);
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int q = q0 + lane + 32 * u;
-                if (va[u] == kRingUnset) va[u] = ld_relaxed_u64(slot + 2 * q);
-                if (vb[u] == kRingUnset) vb[u] = ld_relaxed_u64(slot + 2 * q + 1);
-            }
-            if ((spin & 255u) == 255u) {
-                int bad = 0;
-                if (lane == 0) {
-                    if (t0 == 0) t0 = global_ns();
-                    if (ld_volatile_i32(status) != 0) {
-                        bad = 1;
-                    } else if (global_ns() - t0 > kWaitLimitNs) {
-                        atomicCAS(status, 0, (int)BL_ETIMEOUT);
-                        bad = 1;
-                    }
-                }
-                if (__shfl_sync(0xffffffffu, bad, 0)) return false;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int q = q0 + lane + 32 * u;
-            if (q < nq) tile[q] = ring_pair(va[u], vb[u]);
-        }
-    }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    __syncwarp();
-    return true;
-}
 
 // critical rows of batch k in CTA `rank`: local indices [lo, hi)
 __device__ __forceinline__ void crit_range(int k, int BS, int n, int rank, int G, int& lo,
@@ -296,7 +194,6 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     const bool kahan = prm.kahan != 0;
     float2* const buf0 = tk.pos;
     float2* const buf1 = tk.pos_alt;
-    unsigned long long* const ring = snapshot ? nullptr : tk.ring;
 
     // ---- bulk state: blocks of 32 consecutive local rows per warp (so a warp's rows
     //      share few minibatches and whole warps skip columns they do not need);
@@ -304,22 +201,18 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     //      control warp (hardware warp w runs on sub-partition w % 4) -------------------
     const int wslot = (wb + 1) % 4 == 0 ? (NW - NW / 4) + (wb + 1) / 4 - 1
                                          : wb - (wb + 1) / 4;
-    // this warp's piece: row block and halves of every column tile
-    const int pcode = is_ctl ? 0 : (tk.pieces_on ? tk.piece[wb] : (wslot | (3 << 16)));
-    const int blk = pcode & 0xFFFF, hmask = pcode >> 16;
     f32x2 XI[RPT], YI[RPT];
-    float sx[2][RPT], sy[2][RPT], cx[2][RPT], cy[2][RPT];   // per column half
+    float sx[RPT], sy[RPT], cx[RPT], cy[RPT];
     int bi[RPT], lrow[RPT];
 #pragma unroll
     for (int m = 0; m < RPT; m++) {
-        const int li = lane + 32 * (blk + NW * m);
-        const bool v = !is_ctl && hmask != 0 && li < nloc;
+        const int li = lane + 32 * (wslot + NW * m);
+        const bool v = !is_ctl && li < nloc;
         const int i = rank + G * li;
         const float2 p = v ? __ldcg(&buf0[i]) : make_float2(0.f, 0.f);
         XI[m] = pk2(p.x, p.x);
         YI[m] = pk2(p.y, p.y);
-#pragma unroll
-        for (int h = 0; h < 2; h++) sx[h][m] = sy[h][m] = cx[h][m] = cy[h][m] = 0.f;
+        sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
         bi[m] = v ? i / BS : -1;
         lrow[m] = li;
     }
@@ -336,37 +229,29 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         int mlo, mhi;
         need_range<RPT>(need, mlo, mhi);
         if (mlo >= mhi) return;
-        // column pairs; with pieces the halves [0, hp) and [hp, np) + odd column,
-        // without them one pass over the whole tile into the first accumulator
-        const int np = nc >> 1, hp = tk.pieces_on ? (np >> 1) : np;
+        f32x2 AX[RPT], AY[RPT];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            if (!(hmask & (1 << h)) || (h == 1 && !tk.pieces_on)) continue;   // warp-uniform
-            const int q0 = h == 0 ? 0 : hp, q1 = h == 0 ? hp : np;
-            f32x2 AX[RPT], AY[RPT];
+        for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
+        tile_pairs2<RPT>(tile, nc >> 1, mlo, mhi, XI, YI, AX, AY);
 #pragma unroll
-            for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
-            tile_pairs2<RPT>(tile + q0, q1 - q0, mlo, mhi, XI, YI, AX, AY);
-#pragma unroll
-            for (int m = 0; m < RPT; m++) {
-                float a0, a1, b0, b1, xi, yi, dummy;
-                upk2(AX[m], a0, a1);
-                upk2(AY[m], b0, b1);
-                upk2(XI[m], xi, dummy);
-                upk2(YI[m], yi, dummy);
-                float ax = a0 + a1, ay = b0 + b1;
-                if ((h == 1 || !tk.pieces_on) && (nc & 1)) {
-                    const float2 pc = tile_col(tile, nc - 1);
-                    rep_pair(xi, yi, pc.x, pc.y, ax, ay);
-                }
-                if (need[m]) {
-                    if (kahan) {   // compensated across the row's column tiles
-                        kahan_add(sx[h][m], cx[h][m], ax);
-                        kahan_add(sy[h][m], cy[h][m], ay);
-                    } else {
-                        sx[h][m] += ax;
-                        sy[h][m] += ay;
-                    }
+        for (int m = 0; m < RPT; m++) {
+            float a0, a1, b0, b1, xi, yi, dummy;
+            upk2(AX[m], a0, a1);
+            upk2(AY[m], b0, b1);
+            upk2(XI[m], xi, dummy);
+            upk2(YI[m], yi, dummy);
+            float ax = a0 + a1, ay = b0 + b1;
+            if (nc & 1) {
+                const float2 pc = tile_col(tile, nc - 1);
+                rep_pair(xi, yi, pc.x, pc.y, ax, ay);
+            }
+            if (need[m]) {
+                if (kahan) {   // compensated across the row's column tiles
+                    kahan_add(sx[m], cx[m], ax);
+                    kahan_add(sy[m], cy[m], ay);
+                } else {
+                    sx[m] += ax;
+                    sy[m] += ay;
                 }
             }
         }
@@ -422,8 +307,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         __syncthreads();
     }
 
-    // bulk: post the half sums of the rows of batch kk into crep (half h at
-    // crep[h * CR + row]) and restart them
+    // bulk: post the sums of the rows of batch kk into crep and restart them
     auto post_rows = [&](int kk, float2* crep) {
         int lo, hi;
         crit_range(kk, BS, n, rank, G, lo, hi);
@@ -431,12 +315,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         for (int m = 0; m < RPT; m++) {
             const int li = lrow[m];
             if (bi[m] == kk && li >= lo && li < hi) {
-#pragma unroll
-                for (int h = 0; h < 2; h++)
-                    if (hmask & (1 << h)) {
-                        crep[h * CR + li - lo] = make_float2(sx[h][m] - cx[h][m], sy[h][m] - cy[h][m]);
-                        sx[h][m] = sy[h][m] = cx[h][m] = cy[h][m] = 0.f;
-                    }
+                crep[li - lo] = make_float2(sx[m] - cx[m], sy[m] - cy[m]);
+                sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
             }
         }
     };
@@ -468,9 +348,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     // positions of those neighbours (ids in `slot`, landed) into position slot
     // `pslot`, as the step of batch kk reads them (bnew/bold: that step's buffers):
     // batch(j) < kk moved in this iteration (bnew), batch(j) >= kk not yet (bold);
-    // batches kprev and kprev2 come from that step's column tile and the one before
-    // it instead (< 0: no such tile)
-    auto stage_pos = [&](int kk, int kprev, int kprev2, int slot, int pslot, const float2* bnew,
+    // batch kprev comes from the column tile instead (kprev < 0: no tile)
+    auto stage_pos = [&](int kk, int kprev, int slot, int pslot, const float2* bnew,
                          const float2* bold) {
         int lo, hi;
         crit_range(kk, BS, n, rank, G, lo, hi);
@@ -481,7 +360,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         for (int f = lane; f < tot; f += 32) {
             const int j = cid[f];
             const int bj = j / BS;
-            if ((kprev >= 0 && bj == kprev) || (kprev2 >= 0 && bj == kprev2)) continue;
+            if (kprev >= 0 && bj == kprev) continue;
             cp_async8(&nbr[f], bj < kk ? bnew + j : bold + j);
         }
         cp_async_commit();
@@ -493,10 +372,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     // more than 32 edges: the whole warp). Lane r then moves row r (or records the
     // snapshot force). Returns this lane's energy contribution.
     int cur_s = 0;   // step being traced (control warp)
-    // kprev2 / ptile: the batch of the previous step's tile and that tile (kprev2 < 0: none)
-    auto ctl_critical = [&](int k, int kprev, int kprev2, int slot, int pslot, const float4* tile,
-                            const float4* ptile, float stepf, const float2* bnew, const float2* bold,
-                            const float2* crep, float2* out, unsigned long long* rslot) -> double {
+    auto ctl_critical = [&](int k, int kprev, int slot, int pslot, const float4* tile,
+                            float stepf, const float2* bnew, const float2* bold,
+                            const float2* crep, float2* out) -> double {
         int lo, hi;
         crit_range(k, BS, n, rank, G, lo, hi);
         const int* off = s_off + slot * (CR + 1);
@@ -504,15 +382,11 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         const float2* nbr = s_nbr + (size_t)pslot * CAP;
         const int kplo = kprev >= 0 ? kprev * BS : 0;
         const int kpn = kprev >= 0 ? min(BS, n - kplo) : 0;
-        const int kplo2 = kprev2 >= 0 ? kprev2 * BS : 0;
-        const int kpn2 = kprev2 >= 0 && kprev2 != kprev ? min(BS, n - kplo2) : 0;
         auto nbr_pos = [&](int c, int ee, int e0) -> float2 {
             const int f = off[c] + (ee - e0);
             const int j = f < CAP ? cid[f] : __ldg(&tk.colids[ee]);
             const unsigned o = (unsigned)(j - kplo);
             if (o < (unsigned)kpn) return tile_col(tile, (int)o);
-            const unsigned o2 = (unsigned)(j - kplo2);
-            if (o2 < (unsigned)kpn2) return tile_col(ptile, (int)o2);
             if (f < CAP) return nbr[f];
             return __ldcg(j < k * BS ? bnew + j : bold + j);
         };
@@ -527,18 +401,10 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             float rx = 0.f, ry = 0.f;
             if (g < nr) {   // unrolled: the loads and reciprocals of 8 columns overlap
                 const float2 me = s_pos[lo + c0 + g];
-                if (prm.ctl_nr) {   // off the SFU, which the bulk warps keep busy (uniform)
 #pragma unroll 8
-                    for (int q = gl; q < kpn; q += W) {
-                        const float2 pc = tile_col(tile, q);
-                        rep_pair_nr(me.x, me.y, pc.x, pc.y, rx, ry);
-                    }
-                } else {
-#pragma unroll 8
-                    for (int q = gl; q < kpn; q += W) {
-                        const float2 pc = tile_col(tile, q);
-                        rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
-                    }
+                for (int q = gl; q < kpn; q += W) {
+                    const float2 pc = tile_col(tile, q);
+                    rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
                 }
             }
             for (int o = W >> 1; o > 0; o >>= 1) {
@@ -597,9 +463,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 if (e1 - e0 > 32) {
                     ax = hax_g; ay = hay_g; qx = hqx_g; qy = hqy_g;
                 }
-                // the two column halves of the bulk sums, in order
-                float sxr = crep[c].x + crep[CR + c].x, cxr = 0.f;
-                float syr = crep[c].y + crep[CR + c].y, cyr = 0.f;
+                float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
                 if (kprev >= 0) {
                     if (kahan) {
                         kahan_add(sxr, cxr, rxs);
@@ -629,7 +493,6 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     }
                     out[i] = make_float2(nx, ny);
                     s_pos[li] = make_float2(nx, ny);
-                    if (rslot != nullptr) ring_publish(rslot + (i - k * BS), nx, ny);
                     e += (double)fmaf(fx, fx, fy * fy);   // |ct|^2 in FP32, summed in FP64
                 }
             }
@@ -645,12 +508,12 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 stage_ids(k, 0);
                 cp_async_wait_all();
                 __syncwarp();
-                stage_pos(k, -1, -1, 0, 0, buf0, buf0);
+                stage_pos(k, -1, 0, 0, buf0, buf0);
                 cp_async_wait_all();
                 __syncwarp();
             }
             __syncthreads();
-            if (is_ctl) ctl_critical(k, -1, -1, 0, 0, s_tile, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out, nullptr);
+            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out);
             __syncthreads();
         }
         return;
@@ -665,7 +528,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         if (S > 1) stage_ids(1 % B, 1);
         cp_async_wait_all();
         __syncwarp();
-        stage_pos(0, -1, -1, 0, 0, buf1, buf0);
+        stage_pos(0, -1, 0, 0, buf1, buf0);
         cp_async_wait_all();
         __syncwarp();
     }
@@ -684,19 +547,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             float4* tile = s_tile + (size_t)(s & 1) * TQ;
             cur_s = s;
             if (lane == 0) trace_mark(tk, rank, s, 0);
-            if (s > 0 && ring != nullptr) {
-                // batch kprev from its ring slot (published at step s-1): waiting for
-                // it and copying the tile are one round trip
-                const int nc = min(BS, n - kprev * BS);
-                const bool ok = ring_tile(ring + (size_t)((s - 1) % kRingSlots) * BS, nc, tile, lane, prm.status);
-                if (lane == 0) trace_mark(tk, rank, s, 1);
-                if (!ok) {
-                    s_ctl[0] = 1;                 // tell the bulk warps to leave
-                    bar_sync_n(kBarDone, T);      // their step s-1 is over
-                    bar_arrive_n(kBarTile, T);
-                    return;
-                }
-            } else if (s > 0) {
+            if (s > 0) {
                 // wait until every CTA has published batch kprev (bounded)
                 int ok = 1;
                 if (lane == 0) {
@@ -725,7 +576,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                     return;
                 }
             }
-            if (s == 0 || ring == nullptr) {
+            {
                 // the buffer batch kprev was written to at step s-1 (step 0: the
                 // launch's start positions)
                 const float2* bprev = s == 0 ? buf0 : ((k == 0) ? bold : bnew);
@@ -755,25 +606,12 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (s > 0) bar_sync_n(kBarDone, T);   // bulk finished step s-1
             if (lane == 0) trace_mark(tk, rank, s, 3);
             bar_arrive_n(kBarTile, T);            // bulk may start step s
-            const int kprev2 = s > 0 ? ((k - 2) % B + B) % B : -1;   // batch of step s-1's tile
-            const double e = ctl_critical(k, kprev, kprev2, s % 3, s & 1, tile,
-                                          s_tile + (size_t)((s + 1) & 1) * TQ, (float)step, bnew, bold,
-                                          s_crep + (size_t)(s & 1) * 2 * CR, bnew,
-                                          ring != nullptr ? ring + (size_t)(s % kRingSlots) * BS : nullptr);
+            const double e = ctl_critical(k, kprev, s % 3, s & 1, tile, (float)step, bnew, bold,
+                                          s_crep + (size_t)(s & 1) * CR, bnew);
             if (lane == 0) trace_mark(tk, rank, s, 4);
             e_iter += e;
             __syncwarp();
-            if (ring != nullptr) {
-                // this CTA's share of the ring slot of step s-2 back to unset: every CTA
-                // has read it (they all published step s-1 after reading it), and it is
-                // written again at step s+2, after this CTA's step s+1 publication
-                if (s >= 2) {
-                    unsigned long long* old = ring + (size_t)((s - 2) % kRingSlots) * BS;
-                    for (int q = rank + G * lane; q < BS; q += G * 32) st_relaxed_u64(old + q, kRingUnset);
-                }
-                __syncwarp();
-                if (lane == 0) trace_mark(tk, rank, s, 6);
-            } else if (lane == 0) {
+            if (lane == 0) {
                 red_release_add_u32(prm.bar, 1u);   // this CTA's part of batch k is out
                 trace_mark(tk, rank, s, 6);
             }
@@ -806,7 +644,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (is_stager && s + 1 < S) {   // neighbours of step s+1, ids of step s+2
                 const int kn = (k + 1) % B;
                 const int itn = kn == 0 ? it + 1 : it;
-                stage_pos(kn, k, (k + B - 1) % B, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1,
+                stage_pos(kn, k, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1,
                           (itn & 1) ? buf1 : buf0);
                 if (s + 2 < S) stage_ids((k + 2) % B, (s + 2) % 3);
             }
@@ -817,7 +655,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 need[m] = bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
             if (tb == 0) trace_mark(tk, rank, s, 10);
             add_tile(tile, kpn, need);
-            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * 2 * CR);
+            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * CR);
             if (is_stager) cp_async_wait_all();   // staged data lands before "done"
             if (tb == 0) trace_mark(tk, rank, s, 8);
             bar_arrive_n(kBarDone, T);
@@ -864,8 +702,6 @@ static bl_status launch_grid_t(const ExactPlan& pl, const ExactTask& tk, const E
     if (pl.G > occ * device_sm_count())
         return set_error(BL_EINVAL, "exact engine: grid exceeds co-resident CTAs");
     ExactTask t = tk;
-    t.pieces_on = pl.pieces_on;
-    for (int w = 0; w < 16; w++) t.piece[w] = pl.piece[w];
     ExactParams p = prm;
     void* args[] = {&t, &p};
     BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(pl.G), dim3(T), args, smem, st));
@@ -896,44 +732,6 @@ static bl_status dispatch_rpt(const ExactPlan& pl, const ExactTask& tk, const Ex
 // bulk rounded up to whole warps (256, 320, 384, 448 or 512 threads) so that few
 // lanes idle in the pair loop; up to 2048 rows 512 threads x 2..4 rows, beyond
 // that 256 threads x 6..8 rows.
-// Bulk pieces for one row per thread: the nb row blocks of 32 rows are 2 nb half
-// units (a block over one half of every column tile); each sub-partition gets an
-// equal share (the one the control warp shares gets the smaller one when they
-// cannot be equal), as whole blocks plus at most one half, and a split block's two
-// halves go to two sub-partitions. Bulk warp w runs on sub-partition (w + 1) % 4;
-// the half pieces go to each sub-partition's last warps (on sub-partition 0 that
-// is the warp that also stages neighbours). Off (0) when it does not fit.
-static int plan_pieces(int nloc, int T, int* piece) {
-    const int NW = T / 32, per = NW / 4;
-    const int nb = (nloc + 31) / 32;
-    if (NW % 4 != 0 || nb > NW || nb == 0) return 0;
-    int h[4];
-    const int H = 2 * nb;
-    for (int j = 0; j < 4; j++) h[j] = H / 4;
-    for (int j = 1, r = H % 4; r > 0; j = (j % 3) + 1, r--) h[j]++;   // extra halves to 1, 2, 3
-    std::vector<int> warps[4];
-    for (int w = 0; w < NW; w++) warps[(w + 1) % 4].push_back(w);
-    for (int j = 0; j < 4; j++)
-        if (h[j] / 2 + h[j] % 2 > per) return 0;
-    for (int w = 0; w < NW; w++) piece[w] = 0;   // idle
-    int blk = 0;
-    const int order[4] = {1, 2, 3, 0};
-    for (int j : order)
-        for (int f = 0; f < h[j] / 2; f++) piece[warps[j][f]] = blk++ | (3 << 16);
-    int half = 0;   // the rest in halves: first half, then second, of each block in turn
-    for (int j : order)
-        if (h[j] % 2) {
-            piece[warps[j][h[j] / 2]] = (blk + half / 2) | ((half % 2 == 0 ? 1 : 2) << 16);
-            half++;
-        }
-    return (blk + half / 2 == nb && half % 2 == 0) ? 1 : 0;
-}
-
-int exact_ctl_nr() {
-    const char* e = std::getenv("BL_EXACT_CTL_NR");
-    return (e && e[0] == '1') ? 1 : 0;
-}
-
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out) {
     if (n <= 0 || BS <= 0) return set_error(BL_EINVAL, "exact engine: empty problem");
     const int sms = device_sm_count();
@@ -975,12 +773,6 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
     out->G = G;
     out->T = T;
     out->rpt = chosen;
-    out->pieces_on = 0;
-    for (int w = 0; w < 16; w++) out->piece[w] = 0;
-    {
-        const char* e = std::getenv("BL_EXACT_PIECES");   // 1: balanced pieces (column halves)
-        if (chosen == 1 && e && e[0] == '1') out->pieces_on = plan_pieces(nloc, T, out->piece);
-    }
     out->crit_cap = div_up(std::min(BS, n), G) + 1;
     out->nbr_cap = 2048;
     while (EngineSmem(BS, nloc, out->crit_cap, out->nbr_cap, T / 32).total > 200 * 1024 &&

@@ -116,7 +116,6 @@ struct bl_layout {
     bl::Allocator alloc;
     int trace_steps = 0;                // phase trace of the next run (0 = off)
     bl::DevBuf trace;                   // uint64 timestamps
-    bl::DevBuf ring;                    // exact engine's tile ring (kRingSlots x batch)
     int64_t trace_count = 0;            // entries written by the last traced run
     int phase_timing = 0;               // Barnes-Hut phase events on (bl_set_phase_timing)
     double phase_ms[9] = {};            // phase times of the last timed BH run (bl_get_phase_times)
@@ -150,15 +149,7 @@ struct ExactTask {
     int nbr_cap;         // neighbour positions staged in shared memory
     unsigned long long* trace;   // optional phase timestamps [G][trace_steps][kTraceSlots]
     int trace_steps;
-    // bulk work pieces (rows per thread 1): piece[w] = row block | halves << 16 of bulk
-    // warp w, halves bit 0 = the first half of every column tile, bit 1 = the second
-    int pieces_on;
-    int piece[16];
-    // tile ring (null: the step counter instead): kRingSlots x BS 64-bit slots, one
-    // published position each, all-ones until published
-    unsigned long long* ring;
 };
-constexpr int kRingSlots = 4;
 
 struct ExactParams {
     float invK;          // 1/K
@@ -166,7 +157,6 @@ struct ExactParams {
     int repulse_neighbors;
     int am;              // attraction exponent a of the (a,-1) model
     int kahan;           // 1: compensated repulsion sums across column tiles, 0: plain
-    int ctl_nr;          // 1: the control warp's column pass takes reciprocals on the FMA pipe
     int* status;         // device status word
     unsigned* bar;       // step counter (one arrival per CTA per step)
 };
@@ -176,13 +166,8 @@ struct ExactParams {
 struct ExactPlan {
     int G, T, rpt;
     int crit_cap, nbr_cap;   // see ExactTask
-    int pieces_on;           // see ExactTask
-    int piece[16];
 };
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out);
-// Whether the control warp's column pass takes its reciprocals on the FMA pipe
-// (BL_EXACT_CTL_NR=1) or the SFU.
-int exact_ctl_nr();
 
 // Runs task.iters iterations (or the one-snapshot forces when iters == 0) of one
 // graph on the grid engine. After an odd number of iterations the final
@@ -319,35 +304,6 @@ __device__ __forceinline__ void rep_pair(float xi, float yi, float xj, float yj,
     const float dy = yj - yi;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
     const float inv = rcp_sfu(d2);
-    ax = fmaf(dx, inv, ax);
-    ay = fmaf(dy, inv, ay);
-}
-
-// 1/x on the FMA pipe (no SFU), for x > 0 and normal: Newton-Raphson reciprocal
-// iteration y <- y + y (1 - D y) on the mantissa D = x 2^-e in [0.5, 1), started
-// from the linear estimate 48/17 - 32/17 D (relative error at most 1/17, the
-// textbook initial value of Newton-Raphson division); three steps leave an error
-// below (1/17)^8 ~ 1.4e-10 before FP32 rounding. Then scaled back by 2^-e.
-// x >= 2^126 gives 0 (the true result would be denormal and flushed).
-__device__ __forceinline__ float rcp_nr(float x) {
-    const unsigned b = __float_as_uint(x);
-    const int e = (int)(b >> 23);                             // biased exponent of x (x > 0)
-    const float D = __uint_as_float((b & 0x007FFFFFu) | 0x3F000000u);   // x's mantissa in [0.5, 1)
-    float y = fmaf(-32.0f / 17.0f, D, 48.0f / 17.0f);
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const float r = fmaf(-D, y, 1.0f);
-        y = fmaf(y, r, y);
-    }
-    // x = D 2^(e - 126), so 1/x = y 2^(126 - e): the scale's biased exponent is 253 - e
-    const float scale = __uint_as_float((unsigned)(253 - e) << 23);
-    return e <= 252 ? y * scale : 0.0f;
-}
-__device__ __forceinline__ void rep_pair_nr(float xi, float yi, float xj, float yj, float& ax, float& ay) {
-    const float dx = xj - xi;
-    const float dy = yj - yi;
-    const float d2 = fmaf(dx, dx, fmaf(dy, dy, BL_EPS2));
-    const float inv = rcp_nr(d2);
     ax = fmaf(dx, inv, ax);
     ay = fmaf(dy, inv, ay);
 }

@@ -144,7 +144,6 @@ extern "C" bl_status bl_layout_run_noalloc(int32_t n, const int32_t* d_rowptr, c
     prm.repulse_neighbors = p.repulse_neighbors;
     prm.am = model_exponent(p.energy_model);
     prm.kahan = kahan_on(p.kahan, n) ? 1 : 0;
-    prm.ctl_nr = exact_ctl_nr();
     prm.status = reinterpret_cast<int*>(sc);
     prm.bar = reinterpret_cast<unsigned*>(sc + 64);
     BL_TRY(exact_launch(plan, tk, prm, st));

@@ -187,15 +187,6 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     if (!snapshot) {
         BL_TRY(L->epart.ensure(L->alloc, (size_t)iters * plan.G * sizeof(double)));
         tk.e_iter = L->epart.as<double>();
-        // the tile ring, when every minibatch has a row on every CTA (BL_EXACT_RING=0: the counter)
-        const int last = n - (tk.B - 1) * BS;
-        const char* e = std::getenv("BL_EXACT_RING");
-        if (BS >= plan.G && last >= plan.G && !(e && e[0] == '0')) {
-            const size_t rb = (size_t)kRingSlots * BS * sizeof(unsigned long long);
-            BL_TRY(L->ring.ensure(L->alloc, rb));
-            BL_CUDA_TRY(cudaMemsetAsync(L->ring.p, 0xFF, rb, st));
-            tk.ring = L->ring.as<unsigned long long>();
-        }
     }
     ExactParams prm{};
     prm.invK = 1.0f / L->prm.K;
@@ -203,7 +194,6 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
     prm.repulse_neighbors = L->prm.repulse_neighbors;
     prm.am = model_exponent(L->prm.energy_model);
     prm.kahan = kahan_on(L->prm.kahan, n) ? 1 : 0;
-    prm.ctl_nr = exact_ctl_nr();
     prm.status = static_cast<int*>(L->status.p);
     prm.bar = layout_barrier_word(L);
     BL_TRY(layout_reset_sync_words(L, st));
@@ -230,7 +220,6 @@ void layout_destroy(bl_layout* L) {
     L->status.release();
     L->scratch.release();
     L->trace.release();
-    L->ring.release();
     delete L;
 }
 
