@@ -851,8 +851,10 @@ struct TaskPre {
     int j[4];
 };
 
-__device__ __forceinline__ void task_prefetch(const SweepArgs& a, int t, int lane, TaskPre& p) {
-    p.tk = a.tasks[t];
+// The static data of a task whose record `rec` is already in registers (the
+// records are loaded one task earlier still, so no load here waits on another).
+__device__ __forceinline__ void task_prefetch_rec(const SweepArgs& a, int4 rec, int lane, TaskPre& p) {
+    p.tk = rec;
     const int i = p.tk.x;
     p.me = a.bold[i];
     p.rp = row_rep(a, i);
@@ -970,18 +972,24 @@ __global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepA
     int lnext = l0;   // trace: next level whose first task this warp may meet
     if (a.trace && gw == 0 && lane == 0)
         for (int q = 0; q < l0; q++) a.trace[q] = global_ns();
+    // software pipeline over this warp's tasks t, t+nw, t+2nw, ...: while task t runs,
+    // the static data of task t+nw is in flight and the record of task t+2nw too
     TaskPre cur;
-    if (t < t1) task_prefetch(a, t, lane, cur);
+    const int4 none = make_int4(0, 0, 0, 0);
+    if (t < t1) task_prefetch_rec(a, a.tasks[t], lane, cur);
+    int4 rec1 = t + nw < t1 ? a.tasks[t + nw] : none;
     for (; t < t1; t += nw) {
         if (a.trace && lane == 0) {
             while (lnext < a.nlevels && a.lvl_ptr[lnext] < t) lnext++;
             if (lnext < a.nlevels && a.lvl_ptr[lnext] == t) a.trace[lnext] = global_ns();
         }
+        const int4 rec2 = t + 2 * nw < t1 ? a.tasks[t + 2 * nw] : none;   // two tasks ahead
         TaskPre nxt;
         const bool more = t + nw < t1;
-        if (more) task_prefetch(a, t + nw, lane, nxt);   // static data of the next task
+        if (more) task_prefetch_rec(a, rec1, lane, nxt);   // static data of the next task
         if (!task_run_df(a, cur, lane)) return;
         if (more) cur = nxt;
+        rec1 = rec2;
     }
     if (a.trace && lane == 0) atomicMax(&a.trace[a.nlevels], (unsigned long long)global_ns());
 }
@@ -1261,6 +1269,8 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         BL_CUDA_TRY(cudaEventRecord(s->ev_in, caller));
         BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_in, 0));
     }
+    const char* ea = std::getenv("BL_BH_EDGE_AT");
+    const bool edge_at_walk = ea && ea[0] == 'w';
     PhaseEvents pe;
     if (L->phase_timing) BL_CUDA_TRY(pe.create(iters));
     auto mark = [&](int t, int q, cudaStream_t on) -> cudaError_t {
@@ -1277,28 +1287,35 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         // graph, so it runs while the tree of S is built and walked
         const int rn = L->prm.repulse_neighbors;
         const int am = model_exponent(L->prm.energy_model);
-        BL_CUDA_TRY(cudaEventRecord(s->ev_fork, st));
-        BL_CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-        BL_CUDA_TRY(mark(t, 8, s->side));
-        edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, s->side>>>(
-            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
-            rn, s->old.as<float2>(), s->corr.as<float2>());
-        if (s->nmid > 0)
-            edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, s->side>>>(
-                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->midrows.as<int>(),
-                s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
-        if (s->nbig > 0)
-            edge_pass_big_kernel<<<s->nbig, 1024, 0, s->side>>>(
-                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
-                1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
-        BL_CUDA_TRY(mark(t, 9, s->side));
-        BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
-        BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
-        BL_CUDA_TRY(cudaGetLastError());
-        BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
+        auto launch_edge_pass = [&]() -> bl_status {
+            BL_CUDA_TRY(cudaEventRecord(s->ev_fork, st));
+            BL_CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+            BL_CUDA_TRY(mark(t, 8, s->side));
+            edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, s->side>>>(
+                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
+                rn, s->old.as<float2>(), s->corr.as<float2>());
+            if (s->nmid > 0)
+                edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, s->side>>>(
+                    L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->midrows.as<int>(),
+                    s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
+            if (s->nbig > 0)
+                edge_pass_big_kernel<<<s->nbig, 1024, 0, s->side>>>(
+                    L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
+                    1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
+            BL_CUDA_TRY(mark(t, 9, s->side));
+            BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
+            BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
+            BL_CUDA_TRY(cudaGetLastError());
+            BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
+            return BL_OK;
+        };
+        // edge pass at iteration start (alongside the sort and tree build) or, with
+        // BL_BH_EDGE_AT=walk, when the walk starts (alongside the walk)
+        if (!edge_at_walk) BL_TRY(launch_edge_pass());
         // main stream: the tree of S and its walk
         BL_TRY(bh_build(L, S, st, pe.at(t) ? pe.at(t) + 1 : nullptr));
         BL_CUDA_TRY(mark(t, 3, st));
+        if (edge_at_walk) BL_TRY(launch_edge_pass());
         BL_TRY(bh_repulsion(L, S, theta, st, false));
         BL_CUDA_TRY(mark(t, 4, st));
         BL_TRY(layout_reset_sync_words(L, st));
