@@ -358,9 +358,12 @@ bl_status bl_debug_bh_counts(bl_layout *L, float theta, int32_t *far, int32_t *n
  * published by all CTAs, 2 column tile in shared memory, 3 bulk warps done with
  * the previous step, 9 first critical rows' column pass summed, 11 their CSR
  * terms summed, 4 critical rows moved, 6 arrival posted}; bulk warps {7 step
- * start, 5 moved rows picked up, 10 neighbours staged, 8 step done}. In BH mode (any max_steps > 0) the last
- * iteration's sweep is traced instead: the start time of each of its dependency
- * levels, then its end. */
+ * start, 5 moved rows picked up, 10 neighbours staged, 8 step done}. In BH mode
+ * (any max_steps > 0) the last iteration's sweep is traced instead: the start
+ * time of each of its dependency levels, then its end; with max_steps >= 2 these
+ * are followed by three stamps per sweep task, in the sweep's task order (levels
+ * in order, rows in id order within a level, long rows as consecutive segments):
+ * {task start, its first earlier-minibatch positions gathered, task done}. */
 bl_status bl_set_trace(bl_layout *L, int32_t max_steps);
 
 /* Phase timing of Barnes-Hut runs (profiling; the paper has no counterpart).
@@ -376,7 +379,8 @@ bl_status bl_set_phase_timing(bl_layout *L, int32_t on);
 bl_status bl_get_phase_times(const bl_layout *L, double *out, int64_t cap);
 
 /* Copies the trace of the last traced run: [CTAs][max_steps][12] uint64
- * (exact mode) or [levels + 1] uint64 (BH mode).
+ * (exact mode) or [levels + 1] uint64, then [tasks][3] with max_steps >= 2
+ * (BH mode).
  * *count = entries; with out == NULL only the count. Synchronises. */
 bl_status bl_get_trace(const bl_layout *L, uint64_t *out, int64_t cap, int64_t *count);
 

@@ -68,6 +68,7 @@ struct BHState {
     DevBuf walkcnt;                     // unsigned long long[3]: far nodes, near pairs, warp visits
     // sweep
     int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, nmid = 0, lvl0_rows = 0;
+    int64_t ntasks = 0;
     DevBuf split, bigrows, midrows, old;   // row split points, long and medium rows, old attraction
     DevBuf corr;                        // float2[n]: exact repulsion of the CSR neighbours at S
     DevBuf lvl_ptr, tasks, seg_off, seg_sum, seg_cnt;   // level-set schedule
@@ -788,6 +789,7 @@ struct SweepArgs {
     int am;                  // attraction exponent a of the (a,-1) model
     float invK, negRK2, stepf;
     unsigned long long* trace;   // optional: start time of each level (CTA 0)
+    unsigned long long* ttrace;  // optional: per task {start, neighbours gathered, done}
 };
 
 constexpr int kSegEdges = 128;   // earlier-minibatch edges per task (4 gathers per lane)
@@ -917,8 +919,9 @@ __device__ __forceinline__ bool gather_wait(const SweepArgs& a, Gather4& g, int 
     }
 }
 
-__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane) {
+__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane, int t) {
     const int i = p.tk.x;
+    if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t] = global_ns();
     const int seg = p.tk.w & 0xFFFF, nseg = p.tk.w >> 16;
     const float2 me = p.me;
     float sx = 0.f, sy = 0.f;
@@ -927,6 +930,7 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
     for (int k = 0; k < 4; k++) g.j[k] = p.j[k];
     for (int e = p.tk.y + lane;;) {
         if (!gather_wait(a, g, lane)) return false;
+        if (a.ttrace && lane == 0 && e == p.tk.y) a.ttrace[3 * (size_t)t + 1] = global_ns();
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (g.j[k] >= 0) attr_term(me, unpack_pos(g.v[k]), a.invK, a.am, sx, sy);
@@ -955,6 +959,7 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
                 finish_row(a, i, me, p.rp, p.od, tx, ty);
             }
         }
+        if (a.ttrace) a.ttrace[3 * (size_t)t + 2] = global_ns();
     }
     return true;
 }
@@ -987,7 +992,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepA
         TaskPre nxt;
         const bool more = t + nw < t1;
         if (more) task_prefetch_rec(a, rec1, lane, nxt);   // static data of the next task
-        if (!task_run_df(a, cur, lane)) return;
+        if (!task_run_df(a, cur, lane, t)) return;
         if (more) cur = nxt;
         rec1 = rec2;
     }
@@ -1221,6 +1226,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     s->plan_bs = BS;
     s->plan_seg = segE;
     s->lvl0_rows = nlev > 0 ? lvl_ptr[1] : 0;
+    s->ntasks = (int64_t)tasks.size();
     return BL_OK;
 }
 
@@ -1269,8 +1275,6 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         BL_CUDA_TRY(cudaEventRecord(s->ev_in, caller));
         BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_in, 0));
     }
-    const char* ea = std::getenv("BL_BH_EDGE_AT");
-    const bool edge_at_walk = ea && ea[0] == 'w';
     PhaseEvents pe;
     if (L->phase_timing) BL_CUDA_TRY(pe.create(iters));
     auto mark = [&](int t, int q, cudaStream_t on) -> cudaError_t {
@@ -1287,35 +1291,28 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         // graph, so it runs while the tree of S is built and walked
         const int rn = L->prm.repulse_neighbors;
         const int am = model_exponent(L->prm.energy_model);
-        auto launch_edge_pass = [&]() -> bl_status {
-            BL_CUDA_TRY(cudaEventRecord(s->ev_fork, st));
-            BL_CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-            BL_CUDA_TRY(mark(t, 8, s->side));
-            edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, s->side>>>(
-                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
-                rn, s->old.as<float2>(), s->corr.as<float2>());
-            if (s->nmid > 0)
-                edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, s->side>>>(
-                    L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->midrows.as<int>(),
-                    s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
-            if (s->nbig > 0)
-                edge_pass_big_kernel<<<s->nbig, 1024, 0, s->side>>>(
-                    L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
-                    1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
-            BL_CUDA_TRY(mark(t, 9, s->side));
-            BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
-            BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
-            BL_CUDA_TRY(cudaGetLastError());
-            BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
-            return BL_OK;
-        };
-        // edge pass at iteration start (alongside the sort and tree build) or, with
-        // BL_BH_EDGE_AT=walk, when the walk starts (alongside the walk)
-        if (!edge_at_walk) BL_TRY(launch_edge_pass());
+        BL_CUDA_TRY(cudaEventRecord(s->ev_fork, st));
+        BL_CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        BL_CUDA_TRY(mark(t, 8, s->side));
+        edge_pass_kernel<<<div_up((int64_t)n * 8, 256), 256, 0, s->side>>>(
+            L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, n, 1.0f / L->prm.K, am,
+            rn, s->old.as<float2>(), s->corr.as<float2>());
+        if (s->nmid > 0)
+            edge_pass_mid_kernel<<<div_up((int64_t)s->nmid * 32, 256), 256, 0, s->side>>>(
+                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->midrows.as<int>(),
+                s->nmid, 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
+        if (s->nbig > 0)
+            edge_pass_big_kernel<<<s->nbig, 1024, 0, s->side>>>(
+                L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
+                1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
+        BL_CUDA_TRY(mark(t, 9, s->side));
+        BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
+        BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
+        BL_CUDA_TRY(cudaGetLastError());
+        BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
         // main stream: the tree of S and its walk
         BL_TRY(bh_build(L, S, st, pe.at(t) ? pe.at(t) + 1 : nullptr));
         BL_CUDA_TRY(mark(t, 3, st));
-        if (edge_at_walk) BL_TRY(launch_edge_pass());
         BL_TRY(bh_repulsion(L, S, theta, st, false));
         BL_CUDA_TRY(mark(t, 4, st));
         BL_TRY(layout_reset_sync_words(L, st));
@@ -1340,12 +1337,17 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         a.negRK2 = -L->prm.R * L->prm.K * L->prm.K;
         a.stepf = (float)step;
         a.trace = nullptr;
+        a.ttrace = nullptr;
         if (L->trace_steps > 0 && t == iters - 1) {   // trace the last iteration's sweep
-            const size_t tb = (size_t)(s->nlevels + 1) * sizeof(unsigned long long);
+            const int64_t ntasks = s->ntasks;
+            const bool per_task = L->trace_steps >= 2;
+            const size_t cnt = (size_t)(s->nlevels + 1) + (per_task ? 3 * (size_t)ntasks : 0);
+            const size_t tb = cnt * sizeof(unsigned long long);
             BL_TRY(L->trace.ensure(L->alloc, tb));
             BL_CUDA_TRY(cudaMemsetAsync(L->trace.p, 0, tb, st));
             a.trace = L->trace.as<unsigned long long>();
-            L->trace_count = s->nlevels + 1;
+            if (per_task) a.ttrace = a.trace + (s->nlevels + 1);
+            L->trace_count = (int64_t)cnt;
         }
         a.first_level = s->nlevels > 0 ? 1 : 0;
         BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
