@@ -69,9 +69,10 @@ struct BHState {
     // sweep
     int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, nmid = 0, lvl0_rows = 0;
     int64_t ntasks = 0;
+    int nsegsum = 0;                    // segment slots of the rows of several segments
     DevBuf split, bigrows, midrows, old;   // row split points, long and medium rows, old attraction
     DevBuf corr;                        // float2[n]: exact repulsion of the CSR neighbours at S
-    DevBuf lvl_ptr, tasks, seg_off, seg_sum, seg_cnt;   // level-set schedule
+    DevBuf lvl_ptr, tasks, seg_off, seg_sum;   // level-set schedule; segment partial sums
     DevBuf e_row, epart;                // per-row |ct|^2, reduction partials
     // the edge pass runs on a side stream while the tree is built and walked
     cudaStream_t side = nullptr;
@@ -90,7 +91,7 @@ void bh_state_free(BHState* s) {
                       &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
                       &s->lvl_nodes, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->midrows, &s->old,
                       &s->corr,
-                      &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->seg_cnt, &s->e_row,
+                      &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->e_row,
                       &s->epart};
     for (DevBuf* b : bufs) b->release();
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
@@ -780,8 +781,7 @@ struct SweepArgs {
     const int* lvl_ptr;      // tasks of level l: [lvl_ptr[l], lvl_ptr[l+1])
     const int4* tasks;       // {row, first edge, end edge, segment | nseg << 16}
     const int* seg_off;      // per row: offset of its segment sums (rows with nseg > 1)
-    float2* seg_sum;
-    int* seg_cnt;            // per row: segments finished (reset per launch)
+    float2* seg_sum;         // per row: partial sums of its segments 1.., all-ones until published
     double* e_row;           // |ct|^2 of every row
     int* status;
     int nlevels;
@@ -793,6 +793,7 @@ struct SweepArgs {
 };
 
 constexpr int kSegEdges = 128;   // earlier-minibatch edges per task (4 gathers per lane)
+constexpr int kMaxSeg = 257;     // segments of one row (segment 0's warp reads the other 256)
 
 // New positions are published with one 64-bit store (single-copy atomic), and
 // before the sweep every slot holds kUnset (two NaNs no position can take): a
@@ -850,6 +851,7 @@ __device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float2 me,
 struct TaskPre {
     int4 tk;
     float2 me, rp, od;
+    int off;   // the row's first segment slot (rows of several segments)
     int j[4];
 };
 
@@ -861,6 +863,7 @@ __device__ __forceinline__ void task_prefetch_rec(const SweepArgs& a, int4 rec, 
     p.me = a.bold[i];
     p.rp = row_rep(a, i);
     p.od = a.old[i];
+    p.off = (p.tk.w >> 16) > 1 ? a.seg_off[i] : 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int e = p.tk.y + lane + 32 * k;
@@ -919,7 +922,61 @@ __device__ __forceinline__ bool gather_wait(const SweepArgs& a, Gather4& g, int 
     }
 }
 
-__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane, int t) {
+// A later segment's partial sum, published with one 64-bit store (a pair whose bits
+// equal the all-ones unset pattern is stored as canonical NaNs).
+__device__ __forceinline__ void publish_partial(float2* p, float x, float y) {
+    unsigned long long v = (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
+    if (v == kUnset) v = 0x7FFFFFFF7FFFFFFFull;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Segment 0's warp reads the partial sums of segments 1..nseg-1 of its row (lane l
+// takes segments 1 + l + 32 m) until all are published, into scratch[q - 1].
+// Bounded like gather_wait: false when the wait gave up.
+__device__ __forceinline__ bool seg_wait(const SweepArgs& a, int off, int nseg, int lane, float2* scratch) {
+    constexpr int M = (kMaxSeg - 1 + 31) / 32;
+    unsigned long long v[M];
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        const int q = 1 + lane + 32 * m;
+        v[m] = q < nseg ? read_pos(&a.seg_sum[off + q]) : 0ull;
+    }
+    unsigned long long t0 = 0;
+    for (unsigned spin = 0;; ++spin) {
+        bool pending = false;
+#pragma unroll
+        for (int m = 0; m < M; m++) pending |= 1 + lane + 32 * m < nseg && v[m] == kUnset;
+        if (!__any_sync(0xffffffffu, pending)) break;
+        __nanosleep(64);
+#pragma unroll
+        for (int m = 0; m < M; m++) {
+            const int q = 1 + lane + 32 * m;
+            if (q < nseg && v[m] == kUnset) v[m] = read_pos(&a.seg_sum[off + q]);
+        }
+        if ((spin & 127u) == 127u) {
+            int bad = 0;
+            if (lane == 0) {
+                if (t0 == 0) t0 = global_ns();
+                if (ld_volatile_i32(a.status) != 0) bad = 1;
+                else if (global_ns() - t0 > kWaitLimitNs) {
+                    atomicCAS(a.status, 0, (int)BL_ETIMEOUT);
+                    bad = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        const int q = 1 + lane + 32 * m;
+        if (q < nseg) scratch[q - 1] = unpack_pos(v[m]);
+    }
+    __syncwarp();
+    return true;
+}
+
+__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane, int t,
+                                            float2* scratch) {
     const int i = p.tk.x;
     if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t] = global_ns();
     const int seg = p.tk.w & 0xFFFF, nseg = p.tk.w >> 16;
@@ -941,32 +998,32 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
     }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
-    if (lane == 0) {
-        if (nseg <= 1) {
-            finish_row(a, i, me, p.rp, p.od, sx, sy);
-        } else {
-            const int off = a.seg_off[i];
-            a.seg_sum[off + seg] = make_float2(sx, sy);
-            __threadfence();
-            if (atomicAdd(&a.seg_cnt[i], 1) == nseg - 1) {
-                __threadfence();
-                float tx = 0.f, ty = 0.f;
-                for (int q = 0; q < nseg; q++) {   // segments in order
-                    const float2 v = __ldcg(&a.seg_sum[off + q]);
-                    tx += v.x;
-                    ty += v.y;
-                }
-                finish_row(a, i, me, p.rp, p.od, tx, ty);
+    if (nseg <= 1) {
+        if (lane == 0) finish_row(a, i, me, p.rp, p.od, sx, sy);
+    } else if (seg > 0) {
+        // a later segment: its partial sum goes to its slot for segment 0's warp
+        if (lane == 0) publish_partial(&a.seg_sum[p.off + seg], sx, sy);
+    } else {
+        // segment 0 combines: the other partials, read until published, then all of
+        // them summed in segment order from zero
+        if (!seg_wait(a, p.off, nseg, lane, scratch)) return false;
+        if (lane == 0) {
+            float tx = __fadd_rn(0.f, sx), ty = __fadd_rn(0.f, sy);
+            for (int q = 1; q < nseg; q++) {
+                tx += scratch[q - 1].x;
+                ty += scratch[q - 1].y;
             }
+            finish_row(a, i, me, p.rp, p.od, tx, ty);
         }
-        if (a.ttrace) a.ttrace[3 * (size_t)t + 2] = global_ns();
     }
+    if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t + 2] = global_ns();
     return true;
 }
 
 // two CTAs per SM (the launch's shape): the compiler may use 80 registers a thread
 // instead of squeezing to 64 (2.23 -> 2.18 ms per R-MAT 20 iteration)
 __global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepArgs a) {
+    __shared__ float2 s_seg[kSweepThreads / 32][kMaxSeg - 1];   // segment 0's view of the other partials
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -992,7 +1049,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepA
         TaskPre nxt;
         const bool more = t + nw < t1;
         if (more) task_prefetch_rec(a, rec1, lane, nxt);   // static data of the next task
-        if (!task_run_df(a, cur, lane, t)) return;
+        if (!task_run_df(a, cur, lane, t, s_seg[threadIdx.x >> 5])) return;
         if (more) cur = nxt;
         rec1 = rec2;
     }
@@ -1178,7 +1235,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     std::vector<int> nseg(n);
     for (int i = 0; i < n; i++) {
         const int nd = split[i] - rp[i];
-        nseg[i] = std::max(1, div_up(nd, segE));
+        nseg[i] = std::min(kMaxSeg, std::max(1, div_up(nd, segE)));   // longer segments past kMaxSeg
         lcount[level[i]] += nseg[i];
     }
     std::vector<int> lvl_ptr(nlev + 1, 0);   // levels 1..nlev -> slots 0..nlev-1
@@ -1214,7 +1271,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     BL_TRY(up(s->tasks, tasks.data(), tasks.size() * sizeof(int4)));
     BL_TRY(up(s->seg_off, seg_off.data(), seg_off.size() * 4));
     BL_TRY(s->seg_sum.ensure(al, (size_t)std::max(nsegsum, 1) * sizeof(float2)));
-    BL_TRY(s->seg_cnt.ensure(al, (size_t)n * 4));
+
     BL_TRY(s->e_row.ensure(al, (size_t)n * 8));
     BL_TRY(s->epart.ensure(al, 1024 * 8));
     BL_TRY(s->old.ensure(al, (size_t)n * sizeof(float2)));
@@ -1227,6 +1284,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     s->plan_seg = segE;
     s->lvl0_rows = nlev > 0 ? lvl_ptr[1] : 0;
     s->ntasks = (int64_t)tasks.size();
+    s->nsegsum = nsegsum;
     return BL_OK;
 }
 
@@ -1306,7 +1364,8 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
                 L->g->rowptr.as<int>(), L->g->colids.as<int>(), s->split.as<int>(), S, s->bigrows.as<int>(),
                 1.0f / L->prm.K, am, rn, s->old.as<float2>(), s->corr.as<float2>());
         BL_CUDA_TRY(mark(t, 9, s->side));
-        BL_CUDA_TRY(cudaMemsetAsync(s->seg_cnt.p, 0, (size_t)n * 4, s->side));
+        if (s->nsegsum > 0)   // every segment slot unset
+            BL_CUDA_TRY(cudaMemsetAsync(s->seg_sum.p, 0xFF, (size_t)s->nsegsum * sizeof(float2), s->side));
         BL_CUDA_TRY(cudaMemsetAsync(bnew, 0xFF, (size_t)n * sizeof(float2), s->side));   // every slot kUnset
         BL_CUDA_TRY(cudaGetLastError());
         BL_CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
@@ -1328,7 +1387,6 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         a.tasks = s->tasks.as<int4>();
         a.seg_off = s->seg_off.as<int>();
         a.seg_sum = s->seg_sum.as<float2>();
-        a.seg_cnt = s->seg_cnt.as<int>();
         a.e_row = s->e_row.as<double>();
         a.status = static_cast<int*>(L->status.p);
         a.nlevels = s->nlevels;
