@@ -931,9 +931,12 @@ __device__ __forceinline__ void publish_partial(float2* p, float x, float y) {
 }
 
 // Segment 0's warp reads the partial sums of segments 1..nseg-1 of its row (lane l
-// takes segments 1 + l + 32 m) until all are published, into scratch[q - 1].
-// Bounded like gather_wait: false when the wait gave up.
-__device__ __forceinline__ bool seg_wait(const SweepArgs& a, int off, int nseg, int lane, float2* scratch) {
+// takes segments 1 + l + 32 m) until all are published, and sums all nseg of them
+// (its own p0 in lane 0) in a fixed order: each lane its segments in order of m,
+// then a fixed butterfly across the lanes. Bounded like gather_wait: false when the
+// wait gave up.
+__device__ __forceinline__ bool seg_wait(const SweepArgs& a, int off, int nseg, int lane, float p0x,
+                                         float p0y, float& tx, float& ty) {
     constexpr int M = (kMaxSeg - 1 + 31) / 32;
     unsigned long long v[M];
 #pragma unroll
@@ -966,17 +969,22 @@ __device__ __forceinline__ bool seg_wait(const SweepArgs& a, int off, int nseg, 
             if (__shfl_sync(0xffffffffu, bad, 0)) return false;
         }
     }
+    float sx = lane == 0 ? p0x : 0.f, sy = lane == 0 ? p0y : 0.f;
 #pragma unroll
     for (int m = 0; m < M; m++) {
         const int q = 1 + lane + 32 * m;
-        if (q < nseg) scratch[q - 1] = unpack_pos(v[m]);
+        if (q < nseg) {
+            const float2 w = unpack_pos(v[m]);
+            sx += w.x;
+            sy += w.y;
+        }
     }
-    __syncwarp();
+    tx = warp_sum(sx);
+    ty = warp_sum(sy);
     return true;
 }
 
-__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane, int t,
-                                            float2* scratch) {
+__device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p, int lane, int t) {
     const int i = p.tk.x;
     if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t] = global_ns();
     const int seg = p.tk.w & 0xFFFF, nseg = p.tk.w >> 16;
@@ -1004,17 +1012,10 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
         // a later segment: its partial sum goes to its slot for segment 0's warp
         if (lane == 0) publish_partial(&a.seg_sum[p.off + seg], sx, sy);
     } else {
-        // segment 0 combines: the other partials, read until published, then all of
-        // them summed in segment order from zero
-        if (!seg_wait(a, p.off, nseg, lane, scratch)) return false;
-        if (lane == 0) {
-            float tx = __fadd_rn(0.f, sx), ty = __fadd_rn(0.f, sy);
-            for (int q = 1; q < nseg; q++) {
-                tx += scratch[q - 1].x;
-                ty += scratch[q - 1].y;
-            }
-            finish_row(a, i, me, p.rp, p.od, tx, ty);
-        }
+        // segment 0 combines the partials as the other segments publish them
+        float tx, ty;
+        if (!seg_wait(a, p.off, nseg, lane, sx, sy, tx, ty)) return false;
+        if (lane == 0) finish_row(a, i, me, p.rp, p.od, tx, ty);
     }
     if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t + 2] = global_ns();
     return true;
@@ -1023,7 +1024,6 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
 // two CTAs per SM (the launch's shape): the compiler may use 80 registers a thread
 // instead of squeezing to 64 (2.23 -> 2.18 ms per R-MAT 20 iteration)
 __global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepArgs a) {
-    __shared__ float2 s_seg[kSweepThreads / 32][kMaxSeg - 1];   // segment 0's view of the other partials
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepA
         TaskPre nxt;
         const bool more = t + nw < t1;
         if (more) task_prefetch_rec(a, rec1, lane, nxt);   // static data of the next task
-        if (!task_run_df(a, cur, lane, t, s_seg[threadIdx.x >> 5])) return;
+        if (!task_run_df(a, cur, lane, t)) return;
         if (more) cur = nxt;
         rec1 = rec2;
     }
