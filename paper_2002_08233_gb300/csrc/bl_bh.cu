@@ -289,60 +289,138 @@ __global__ void morton_kernel(const float2* __restrict__ pos, int n, const float
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort of (u32 key, i32 value), 8 bits per pass
+// stable LSD radix sort of (u32 key, i32 value): 4 passes of 8 bits, one kernel
+// per pass. One histogram kernel counts every digit of every pass (the counts do
+// not depend on the order); a pass kernel takes tiles in ticket order, ranks each
+// tile's keys by digit in index order (stable), and gets, for every digit, the
+// count of that digit in all earlier tiles by decoupled look-back: each tile
+// publishes its digit counts (flag "aggregate"), then walks back over the earlier
+// tiles' published words, adding aggregates until it meets an inclusive prefix,
+// and publishes its own inclusive prefix (Merrill and Garland's single-pass
+// prefix scan, as used for radix sorting by Adinets and Merrill's Onesweep).
 // ---------------------------------------------------------------------------
 
-__global__ void radix_hist_kernel(const unsigned* __restrict__ keys, int n, int shift, int nblocks,
-                                  int* __restrict__ hist) {
-    __shared__ int s_cnt[256];
-    s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const int base = blockIdx.x * kSortTile;
-    for (int q = 0; q < kSortItems; q++) {
-        const int idx = base + q * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&s_cnt[(keys[idx] >> shift) & 255u], 1);
-    }
-    __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = s_cnt[threadIdx.x];   // digit-major
+constexpr unsigned kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1;
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void radix_scatter_kernel(const unsigned* __restrict__ kin, const int* __restrict__ vin,
-                                     int n, int shift, int nblocks, const int* __restrict__ offs,
-                                     unsigned* __restrict__ kout, int* __restrict__ vout) {
-    constexpr int W = kSortThreads / 32;
-    __shared__ int s_run[256];
-    __shared__ int s_wcnt[W][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    s_run[threadIdx.x] = offs[threadIdx.x * nblocks + blockIdx.x];
-    for (int w = 0; w < W; w++) s_wcnt[w][threadIdx.x] = 0;
+// counts of every digit of every pass into hist[p * 256 + d] (zeroed before)
+__global__ void radix_hist4_kernel(const unsigned* __restrict__ keys, int n, unsigned* __restrict__ hist) {
+    __shared__ unsigned s_h[4 * 256];
+    for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x) s_h[q] = 0u;
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    const int base = blockIdx.x * kSortTile;
-    for (int q = 0; q < kSortItems; q++) {   // chunks in index order: stable
-        const int idx = base + q * kSortThreads + threadIdx.x;
-        const bool valid = idx < n;
-        const unsigned key = valid ? kin[idx] : 0u;
-        const int d = valid ? (int)((key >> shift) & 255u) : 256;   // 256: no digit
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & lt);
-        if (valid && rank == 0) s_wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            int before = 0;
-            for (int w = 0; w < warp; w++) before += s_wcnt[w][d];
-            const int dst = s_run[d] + before + rank;
-            kout[dst] = key;
-            vout[dst] = vin[idx];
-        }
-        __syncthreads();
-        int tot = 0;
-        for (int w = 0; w < W; w++) {
-            tot += s_wcnt[w][threadIdx.x];
-            s_wcnt[w][threadIdx.x] = 0;
-        }
-        s_run[threadIdx.x] += tot;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned k = keys[i];
+#pragma unroll
+        for (int p = 0; p < 4; p++) atomicAdd(&s_h[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 4 * 256; q += blockDim.x)
+        if (s_h[q]) atomicAdd(&hist[q], s_h[q]);
+}
+
+// digit counts -> exclusive digit bases, per pass (one block of 256 threads)
+__global__ void radix_bases_kernel(unsigned* hist) {
+    __shared__ int s_warp[8];
+    for (int p = 0; p < 4; p++) {
+        int total;
+        const int ex = block_exclusive_scan_256((int)hist[p * 256 + threadIdx.x], s_warp, total);
+        hist[p * 256 + threadIdx.x] = (unsigned)ex;
         __syncthreads();
     }
+}
+
+// One pass on digit (key >> shift) & 255. base: the pass's exclusive digit bases;
+// status: [tiles][256] words of this pass and tile_ctr, all zero at launch. pass 0
+// takes its values as the keys' indices (ident). A look-back wait that gives up
+// sets *err to BL_ETIMEOUT (the tile's output is then garbage; the host reports it).
+__global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
+    const unsigned* __restrict__ kin, const int* __restrict__ vin, int n, int shift,
+    const unsigned* __restrict__ base, unsigned* __restrict__ status, unsigned* __restrict__ tile_ctr,
+    int ident, int* __restrict__ err, unsigned* __restrict__ kout, int* __restrict__ vout) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ unsigned s_whist[W][256];   // digit counts per warp, then their exclusive prefix
+    __shared__ unsigned s_dst[256];        // where this tile's keys of each digit start
+    __shared__ int s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);   // tickets in order: the look-back
+#pragma unroll                                                       // only waits on tiles already taken
+    for (int w = 0; w < W; w++) s_whist[w][threadIdx.x] = 0u;
+    __syncthreads();
+    const int tile = s_tile;
+    // the warp's keys: rows of 32 consecutive keys, rows in order
+    const int wbase = tile * kSortTile + warp * 32 * kSortItems;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned key[kSortItems], rk[kSortItems];
+    int val[kSortItems], dg[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        const int idx = wbase + r * 32 + lane;
+        const bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? (ident ? idx : vin[idx]) : 0;
+        dg[r] = valid ? (int)((key[r] >> shift) & 255u) : 256;   // 256: no key
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {   // rank within the warp, in index order
+        const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+        const unsigned before = dg[r] < 256 ? s_whist[warp][dg[r]] : 0u;
+        __syncwarp();
+        if (dg[r] < 256 && (peers & lt) == 0u) s_whist[warp][dg[r]] = before + __popc(peers);
+        __syncwarp();
+        rk[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {   // thread d: digit d's prefix over the warps, the tile's count, and its look-back
+        const int d = threadIdx.x;
+        unsigned tot = 0u;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const unsigned c = s_whist[w][d];
+            s_whist[w][d] = tot;
+            tot += c;
+        }
+        unsigned* my = status + (size_t)tile * 256 + d;
+        unsigned excl = 0u;
+        if (tile == 0) {
+            st_relaxed_u32(my, kFlagInc | tot);
+        } else {
+            st_relaxed_u32(my, kFlagAgg | tot);
+            unsigned long long t0 = 0;
+            for (int pred = tile - 1; pred >= 0;) {
+                const unsigned v = ld_relaxed_u32(status + (size_t)pred * 256 + d);
+                if ((v & ~kCountMask) == 0u) {   // not published yet: bounded wait
+                    __nanosleep(32);
+                    if (t0 == 0) t0 = global_ns();
+                    else if (global_ns() - t0 > kWaitLimitNs) {
+                        atomicCAS(err, 0, (int)BL_ETIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                excl += v & kCountMask;
+                if (v & kFlagInc) break;
+                pred--;
+            }
+            st_relaxed_u32(my, kFlagInc | (excl + tot));
+        }
+        s_dst[d] = base[d] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++)
+        if (dg[r] < 256) {
+            const unsigned dst = s_dst[dg[r]] + s_whist[warp][dg[r]] + rk[r];
+            kout[dst] = key[r];
+            vout[dst] = val[r];
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -1109,7 +1187,9 @@ static bl_status bh_ensure(bl_layout* L) {
     BL_TRY(s->keys1.ensure(al, N * 4));
     BL_TRY(s->vals0.ensure(al, N * 4));
     BL_TRY(s->vals1.ensure(al, N * 4));
-    BL_TRY(s->hist.ensure(al, (size_t)256 * nb_sort * 4));
+    // radix sort: digit counts/bases [4][256], tile tickets [4] (at +1024), then
+    // the look-back words [4][tiles][256]
+    BL_TRY(s->hist.ensure(al, ((size_t)1024 + 64 + (size_t)4 * nb_sort * 256) * 4));
     BL_TRY(s->scan_part.ensure(al, (size_t)(div_up(std::max<int64_t>(cap, (int64_t)256 * nb_sort), kScanItems) + 1) * 4));
     BL_TRY(s->bpart.ensure(al, 1024 * sizeof(float4)));
     BL_TRY(s->box.ensure(al, 32 * sizeof(float)));
@@ -1148,12 +1228,17 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st, cudaEv
     unsigned* kout = s->keys1.as<unsigned>();
     int* vin = s->vals0.as<int>();
     int* vout = s->vals1.as<int>();
+    unsigned* hist = s->hist.as<unsigned>();
+    unsigned* tickets = hist + 1024;
+    unsigned* look = hist + 1024 + 64;
+    BL_CUDA_TRY(cudaMemsetAsync(hist, 0, ((size_t)1024 + 64 + (size_t)4 * nbs * 256) * 4, st));
+    radix_hist4_kernel<<<std::min(nbs * 4, device_sm_count() * 4), 256, 0, st>>>(kin, n, hist);
+    radix_bases_kernel<<<1, 256, 0, st>>>(hist);
     for (int pass = 0; pass < 4; pass++) {
-        const int shift = 8 * pass;
-        radix_hist_kernel<<<nbs, kSortThreads, 0, st>>>(kin, n, shift, nbs, s->hist.as<int>());
-        BL_TRY(exclusive_scan(s->hist.as<int>(), s->hist.as<int>(), 256 * nbs, s->scan_part.as<int>(), st));
-        radix_scatter_kernel<<<nbs, kSortThreads, 0, st>>>(kin, vin, n, shift, nbs, s->hist.as<int>(),
-                                                            kout, vout);
+        radix_pass_kernel<<<nbs, kSortThreads, 0, st>>>(kin, vin, n, 8 * pass, hist + 256 * pass,
+                                                        look + (size_t)pass * nbs * 256, tickets + pass,
+                                                        pass == 0 ? 1 : 0, static_cast<int*>(L->status.p),
+                                                        kout, vout);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
