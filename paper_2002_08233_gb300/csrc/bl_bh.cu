@@ -46,7 +46,7 @@ namespace bl {
 constexpr int kLevels = 16;
 constexpr int kScanItems = 1024;     // elements per block of the scan
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;       // elements per thread of a sort tile
+constexpr int kSortItems = 8;        // elements per thread of a sort tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSweepThreads = 256;
 
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(256) walk_kernel(
             near += (unsigned)cnt;   // leaf vertices visited, the query's own included
             for (int m = 0; m < cnt; m++) {
                 const int k = aux.y + m;
-                if (perm[k] == i) continue;
+                if (k == q) continue;   // the query itself: sorted position q is vertex i
                 const float2 p = cnt == 1 ? make_float2(rec.x, rec.y) : spos[k];
                 float ax = 0.f, ay = 0.f;
                 rep_pair(me.x, me.y, p.x, p.y, ax, ay);
@@ -1410,14 +1410,10 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
     if (const char* e = std::getenv("BL_BH_SWEEP_CTAS")) per_sm = std::max(1, std::atoi(e));
     const int G = std::max(1, std::min(occ, per_sm)) * device_sm_count();
     const int nep = std::min(1024, div_up(n, 1024));
-    // st: the stream of the iteration's critical path (BL_BH_PRIORITY=0: the caller's)
-    const char* pe_env = std::getenv("BL_BH_PRIORITY");
-    const bool use_hi = !(pe_env && pe_env[0] == '0');
-    cudaStream_t st = use_hi ? s->hi : caller;
-    if (use_hi) {
-        BL_CUDA_TRY(cudaEventRecord(s->ev_in, caller));
-        BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_in, 0));
-    }
+    // st: the stream of the iteration's critical path, forked from the caller's
+    cudaStream_t st = s->hi;
+    BL_CUDA_TRY(cudaEventRecord(s->ev_in, caller));
+    BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_in, 0));
     PhaseEvents pe;
     if (L->phase_timing) BL_CUDA_TRY(pe.create(iters));
     auto mark = [&](int t, int q, cudaStream_t on) -> cudaError_t {
@@ -1510,10 +1506,9 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         std::swap(L->pos, L->pos2);
         step *= 0.999;
     }
-    if (use_hi) {   // the caller's stream continues after the iterations
-        BL_CUDA_TRY(cudaEventRecord(s->ev_out, st));
-        BL_CUDA_TRY(cudaStreamWaitEvent(caller, s->ev_out, 0));
-    }
+    // the caller's stream continues after the iterations
+    BL_CUDA_TRY(cudaEventRecord(s->ev_out, st));
+    BL_CUDA_TRY(cudaStreamWaitEvent(caller, s->ev_out, 0));
     // interaction counts of the last iteration
     unsigned long long c[3] = {0, 0, 0};
     int nodes = 0;
