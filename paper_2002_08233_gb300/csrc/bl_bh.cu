@@ -46,7 +46,7 @@ namespace bl {
 constexpr int kLevels = 16;
 constexpr int kScanItems = 1024;     // elements per block of the scan
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;        // elements per thread of a sort tile
+constexpr int kSortItems = 16;       // elements per thread of a sort tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSweepThreads = 256;
 
