@@ -252,9 +252,10 @@ bl_status bl_layout_run_batch(bl_layout *const *Ls, int32_t count, int32_t iters
  * they fit the budget (whole-GPU jobs also need one of 4 slots), then advances
  * every admitted request: exact requests of at most 16,384 vertices, batch
  * <= 256 and n^2 x iters <= 2.5e9 share one persistent batched launch (50
- * iterations per tick); the
- * others (larger exact, and BH) run a chunk whose length depends only on the
- * request. A finished layout is copied to host memory and its device memory
+ * iterations per tick); the others (larger exact, and BH) run a chunk whose
+ * length depends only on the request, each on a stream of its own, so the chunks
+ * and the batched launch of a tick overlap on the device. A finished layout is
+ * copied to host memory and its device memory
  * returns to the budget at once. A request's result does not depend on what
  * else is being served. Device memory comes from the library allocator
  * (bl_set_allocator) in force at each allocation. */

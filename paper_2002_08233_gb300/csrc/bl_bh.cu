@@ -1395,7 +1395,7 @@ struct PhaseEvents {
     cudaEvent_t* at(int t) { return ev.empty() ? nullptr : ev.data() + (size_t)t * kPhaseEvents; }
 };
 
-bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t caller) {
+bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t caller, bool sync) {
     BL_TRY(bh_ensure(L));
     BL_TRY(bh_plan(L, BS, caller));
     BHState* s = L->bh;
@@ -1415,7 +1415,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
     BL_CUDA_TRY(cudaEventRecord(s->ev_in, caller));
     BL_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_in, 0));
     PhaseEvents pe;
-    if (L->phase_timing) BL_CUDA_TRY(pe.create(iters));
+    if (L->phase_timing && sync) BL_CUDA_TRY(pe.create(iters));
     auto mark = [&](int t, int q, cudaStream_t on) -> cudaError_t {
         cudaEvent_t* e = pe.at(t);
         return e ? cudaEventRecord(e[q], on) : cudaSuccess;
@@ -1509,6 +1509,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
     // the caller's stream continues after the iterations
     BL_CUDA_TRY(cudaEventRecord(s->ev_out, st));
     BL_CUDA_TRY(cudaStreamWaitEvent(caller, s->ev_out, 0));
+    if (!sync) return BL_OK;
     // interaction counts of the last iteration
     unsigned long long c[3] = {0, 0, 0};
     int nodes = 0;

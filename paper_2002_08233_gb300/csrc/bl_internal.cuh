@@ -183,7 +183,9 @@ unsigned* layout_barrier_word(bl_layout* L);
 bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, cudaStream_t st);
 
 // Barnes-Hut iterations of one layout (bl_bh.cu); the caller updates L's counters.
-bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st);
+// With sync, waits for the iterations and reads back the last walk's interaction
+// counts (and phase times); without, returns once everything is queued on st.
+bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st, bool sync = true);
 
 // Compensated (Kahan) FP32 repulsion sums: bl_force_params.kahan = 1 always, 0
 // never, < 0 from kKahanAutoN vertices on.

@@ -123,7 +123,7 @@ unsigned* layout_barrier_word(bl_layout* L) {
 }
 
 // BH engine entry points (bl_bh.cu)
-bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t st);
+
 bl_status bh_debug_forces(bl_layout* L, float theta, float2* f_out, cudaStream_t st);
 bl_status bh_debug_counts(bl_layout* L, float theta, int2* qcounts, cudaStream_t st);
 bl_status bh_debug_tree(bl_layout* L, uint32_t* codes, int32_t* perm, int32_t* first,

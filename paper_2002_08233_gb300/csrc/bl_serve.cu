@@ -13,9 +13,14 @@
 // memory and slots free up. A job's chunk boundaries depend only on the job, and
 // both engines give the same positions however the iterations are split, so a
 // result is the same alone and in any mix.
-// The whole-GPU engines rely on all of their CTAs being resident for their
-// grid-wide waits, so they never run next to the persistent batched kernel: a
-// tick issues its launches in order on the worker's stream.
+// Each whole-GPU job has a stream of its own. A tick first queues a chunk of every
+// whole-GPU job, each on its stream, then the batched launch on the worker's
+// stream, and only then waits for them: the jobs' work overlaps on the device
+// (Barnes-Hut iterations of mid-size graphs leave most of the GPU idle while their
+// sweeps wait on dependency chains). The engines' grid-wide waits need all of a
+// kernel's CTAs resident; next to other kernels some may start late, which only
+// delays a wait (every wait is bounded, and the kernels sharing the GPU are
+// chunks of about 25 ms that need nothing from it).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,6 +65,7 @@ struct Job {
     std::string msg;
     Clock::time_point t_submit, t_done;
     std::vector<float> result;
+    cudaStream_t st = nullptr;   // whole-GPU jobs: the job's own stream (else the worker's)
 };
 
 // Working memory a job holds on the device while admitted.
@@ -115,19 +121,24 @@ bl_status read_status(bl_layout* L, cudaStream_t st) {
 
 // Ends a job (done or failed): result to host, device memory back to the budget.
 void retire(bl_server* S, Job* j, bl_status err) {
+    cudaStream_t st = j->st ? j->st : S->st;
     if (err == BL_OK && j->L) {
         j->result.resize(2 * (size_t)j->g->n);
         cudaError_t e = cudaMemcpyAsync(j->result.data(), j->L->pos.p, j->result.size() * sizeof(float),
-                                        cudaMemcpyDeviceToHost, S->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) err = cuda_error(e, "server: result copy");
     }
     if (err != BL_OK && j->msg.empty()) j->msg = bl_last_error();
     if (j->L) {
-        cudaStreamSynchronize(S->st);   // the job's work ran on the server's stream
+        cudaStreamSynchronize(st);   // nothing of the job may still be running
         layout_destroy(j->L);
     }
     j->L = nullptr;
+    if (j->st) {
+        cudaStreamDestroy(j->st);
+        j->st = nullptr;
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     j->t_done = Clock::now();
     S->in_use -= j->bytes;
@@ -167,7 +178,15 @@ void worker_main(bl_server* S) {
             }
         }
         for (Job* j : admitted) {
-            const bl_status s = layout_create(j->g, nullptr, j->seed, 0, nullptr, true, S->st, &j->L);
+            bl_status s = BL_OK;
+            if (!j->small) {
+                const cudaError_t e = cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking);
+                if (e != cudaSuccess) {
+                    j->st = nullptr;
+                    s = cuda_error(e, "server: job stream");
+                }
+            }
+            if (s == BL_OK) s = layout_create(j->g, nullptr, j->seed, 0, nullptr, true, j->st ? j->st : S->st, &j->L);
             if (s != BL_OK) {
                 j->msg = bl_last_error();
                 retire(S, j, s);   // j may be deleted by a poll from here on
@@ -188,7 +207,16 @@ void worker_main(bl_server* S) {
                 }
             }
         }
-        // one tick: the batched launch, then a chunk of each whole-GPU job
+        // one tick: a chunk of each whole-GPU job queued on its stream, then the
+        // batched launch (which waits for its own stream only), then the jobs' ends
+        std::vector<int> its(big.size(), 0);
+        std::vector<bl_status> issued(big.size(), BL_OK);
+        for (size_t q = 0; q < big.size(); q++) {
+            Job* j = big[q];
+            its[q] = std::min(j->chunk, j->iters - j->done);
+            issued[q] = j->mode == BL_EXACT ? exact_run(j->L, its[q], j->BS, false, nullptr, j->st)
+                                            : bh_run(j->L, its[q], j->BS, j->theta, j->st, false);
+        }
         if (!bj.empty()) {
             const bl_status s = batch_launch(bj.data(), (int)bj.size(), 0, S->st);
             for (size_t q = 0; q < bjobs.size(); q++) {
@@ -201,11 +229,11 @@ void worker_main(bl_server* S) {
                 if (j->done >= j->iters) retire(S, j, BL_OK);
             }
         }
-        for (Job* j : big) {
-            const int it = std::min(j->chunk, j->iters - j->done);
-            bl_status s = j->mode == BL_EXACT ? exact_run(j->L, it, j->BS, false, nullptr, S->st)
-                                              : bh_run(j->L, it, j->BS, j->theta, S->st);
-            if (s == BL_OK) s = read_status(j->L, S->st);
+        for (size_t q = 0; q < big.size(); q++) {
+            Job* j = big[q];
+            const int it = its[q];
+            bl_status s = issued[q];
+            if (s == BL_OK) s = read_status(j->L, j->st);
             if (s != BL_OK) {
                 retire(S, j, s);
                 continue;
@@ -227,8 +255,11 @@ void worker_main(bl_server* S) {
     }
     cudaStreamSynchronize(S->st);
     for (Job* j : left) {
+        if (j->st) cudaStreamSynchronize(j->st);
         if (j->L) layout_destroy(j->L);
         j->L = nullptr;
+        if (j->st) cudaStreamDestroy(j->st);
+        j->st = nullptr;
     }
 }
 
