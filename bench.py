@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--batched-iters", type=int, default=300, help="iterations of the batched line")
     ap.add_argument("--bh-scale", type=int, default=20, help="R-MAT scale of the BH line")
     ap.add_argument("--serve-count", type=int, default=32, help="requests of the serving line")
+    ap.add_argument("--serve-rates", default="0.5,0.8,1.0,1.2",
+                    help="offered loads of the serving line, as fractions of the saturated rate")
     return ap.parse_args()
 
 
@@ -647,7 +649,10 @@ def run_serving(args, local):
     thr = len(reqs) / wall_sat
     unit_gaps = np.array([r.arrival_s for r in reqs])   # the seeded unit-rate arrivals
     sweep = {}
-    for f in (0.5, 0.8, 1.0, 1.2):   # offered load as a fraction of the saturated rate
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    if 0.8 not in rates:
+        rates.append(0.8)   # the line's headline latency
+    for f in rates:   # offered load as a fraction of the saturated rate
         lam_f = f * thr
         wall_f, st_f = serve(list(unit_gaps / lam_f))
         sweep[f"{f}x"] = {"rate_per_s": lam_f, "layouts_per_s": len(reqs) / wall_f,

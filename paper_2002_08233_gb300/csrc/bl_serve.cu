@@ -27,6 +27,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -43,7 +44,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kSmallChunk = 50;          // iterations per tick of a batched job
-constexpr int kBigSlots = 4;             // whole-GPU jobs admitted at a time
+constexpr int kBigSlots = 4;             // whole-GPU jobs admitted at a time (BL_SERVE_SLOTS overrides)
 constexpr double kBigChunkMs = 25.0;     // target work per whole-GPU chunk
 constexpr int kAutoExactBelow = 50000;   // BL_AUTO: exact below this many vertices
 constexpr double kBatchedWorkMax = 2.5e9; // n^2 x iterations of a job the batched launch takes
@@ -92,6 +93,7 @@ using namespace bl;
 
 struct bl_server {
     int device = 0;
+    int big_slots = kBigSlots;
     cudaStream_t st = nullptr;
     size_t budget = 0, in_use = 0, peak = 0;
     std::mutex mu;
@@ -167,7 +169,7 @@ void worker_main(bl_server* S) {
             while (!S->queue.empty()) {
                 Job* j = S->queue.front();
                 if (S->in_use + j->bytes > S->budget) break;
-                if (!j->small && big_active >= kBigSlots) break;
+                if (!j->small && big_active >= S->big_slots) break;
                 S->queue.pop_front();
                 S->in_use += j->bytes;
                 S->peak = std::max(S->peak, S->in_use);
@@ -273,6 +275,7 @@ bl_status bl_server_create(size_t mem_budget_bytes, bl_server** out) {
     if (mem_budget_bytes == 0) return set_error(BL_EINVAL, "bl_server_create: budget must be positive");
     bl_server* S = new bl_server();
     S->budget = mem_budget_bytes;
+    if (const char* e = std::getenv("BL_SERVE_SLOTS")) S->big_slots = std::max(1, std::min(64, std::atoi(e)));
     cudaError_t e = cudaGetDevice(&S->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
