@@ -624,8 +624,13 @@ def run_serving(args, local):
     from paper_2002_08233_gb300 import core, synth
     core.load()
     core.use_torch()
-    reqs = synth.serving_stream(count, 1.0, 1e3, 2e6, seed=5)
-    Gs = [core.Graph(r.graph) for r in reqs]
+    # long streams: graphs drawn in parallel (spawn pool) and uploaded as they
+    # arrive, without keeping the host copies
+    workers = min(os.cpu_count() or 1, 16) if count > 64 else 1
+    reqs, Gs = [], []
+    for r in synth.serving_stream(count, 1.0, 1e3, 2e6, seed=5, workers=workers):
+        Gs.append(core.Graph(r.graph))
+        reqs.append(synth.Request(arrival_s=r.arrival_s, graph=None, seed=r.seed))
     budget = 120 * (1 << 30)
 
     def serve(arrivals):

@@ -63,7 +63,7 @@ struct BHState {
     DevBuf nd_rec;                      // float4 {gx, gy, Dl^2, count}
     DevBuf nd_aux;                      // int2 {skip, leaf ? first : -1}
     DevBuf lvl;                         // int[64]: per-level counts, offsets, fill
-    DevBuf lvl_nodes;                   // nodes bucketed by level
+    DevBuf lvl_info;                    // nodes bucketed by level: int4 {node, first, count, skip}
     DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
     DevBuf walkcnt;                     // unsigned long long[3]: far nodes, near pairs, warp visits
     // sweep
@@ -89,7 +89,7 @@ void bh_state_free(BHState* s) {
     DevBuf* bufs[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->hist, &s->scan_part,
                       &s->bpart, &s->box, &s->cnt, &s->spos, &s->nd_first, &s->nd_count,
                       &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
-                      &s->lvl_nodes, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->midrows, &s->old,
+                      &s->lvl_info, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->midrows, &s->old,
                       &s->corr,
                       &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->e_row,
                       &s->epart};
@@ -517,10 +517,13 @@ __global__ void level_offsets_kernel(int* __restrict__ lvl) {
     lvl[20 + kLevels + 1] = acc;
 }
 
-__global__ void level_bucket_kernel(const int* __restrict__ nd_level, const int* __restrict__ first_node,
-                                    int n, int* __restrict__ lvl, int* __restrict__ lvl_nodes) {
+__global__ void level_bucket_kernel(const int* __restrict__ nd_level, const int* __restrict__ nd_first,
+                                    const int* __restrict__ nd_count, const int* __restrict__ nd_skip,
+                                    const int* __restrict__ first_node, int n, int* __restrict__ lvl,
+                                    int4* __restrict__ lvl_info) {
     // each block buckets a contiguous range: count per level in shared memory,
-    // reserve each level's room with one global atomic, then scatter
+    // reserve each level's room with one global atomic, then scatter each node's
+    // build fields (read here in pre-order, so coalesced) into its level's slots
     __shared__ int s_cnt[kLevels + 1], s_base[kLevels + 1];
     const int M = first_node[n];
     const int per = (M + gridDim.x - 1) / gridDim.x;
@@ -537,25 +540,22 @@ __global__ void level_bucket_kernel(const int* __restrict__ nd_level, const int*
     __syncthreads();
     for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         const int l = nd_level[v];
-        lvl_nodes[s_base[l] + atomicAdd(&s_cnt[l], 1)] = v;
+        lvl_info[s_base[l] + atomicAdd(&s_cnt[l], 1)] = make_int4(v, nd_first[v], nd_count[v], nd_skip[v]);
     }
 }
 
-__global__ void level_sums_kernel(int l, const int* __restrict__ lvl, const int* __restrict__ lvl_nodes,
-                                  const float2* __restrict__ spos, const int* __restrict__ nd_first,
-                                  const int* __restrict__ nd_count, const int* __restrict__ nd_skip,
+__global__ void level_sums_kernel(int l, const int* __restrict__ lvl, const int4* __restrict__ lvl_info,
+                                  const float2* __restrict__ spos, const int* __restrict__ nd_skip,
                                   const float* __restrict__ box, float2* __restrict__ nd_sum,
                                   float4* __restrict__ nd_rec, int2* __restrict__ nd_aux) {
     const int lo = lvl[20 + l], hi = lvl[20 + l + 1];
     const float Dl2 = box[4 + l];
     for (int q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) {
-        const int v = lvl_nodes[q];
-        const int cnt = nd_count[v];
-        const int skip = nd_skip[v];
+        const int4 info = lvl_info[q];   // {node, first, count, skip}
+        const int v = info.x, f = info.y, cnt = info.z, skip = info.w;
         const bool leaf = cnt == 1 || l == kLevels;
         float sx, sy;
         if (leaf) {
-            const int f = nd_first[v];
             sx = 0.f;
             sy = 0.f;
             for (int m = 0; m < cnt; m++) {   // vertices in sorted order
@@ -577,7 +577,7 @@ __global__ void level_sums_kernel(int l, const int* __restrict__ lvl, const int*
         nd_sum[v] = make_float2(sx, sy);
         const float fc = (float)cnt;
         nd_rec[v] = make_float4(__fdiv_rn(sx, fc), __fdiv_rn(sy, fc), Dl2, fc);
-        nd_aux[v] = make_int2(skip, leaf ? nd_first[v] : -1);
+        nd_aux[v] = make_int2(skip, leaf ? f : -1);
     }
 }
 
@@ -1203,7 +1203,7 @@ static bl_status bh_ensure(bl_layout* L) {
     BL_TRY(s->nd_rec.ensure(al, (size_t)cap * sizeof(float4)));
     BL_TRY(s->nd_aux.ensure(al, (size_t)cap * sizeof(int2)));
     BL_TRY(s->lvl.ensure(al, 64 * 4));
-    BL_TRY(s->lvl_nodes.ensure(al, (size_t)cap * 4));
+    BL_TRY(s->lvl_info.ensure(al, (size_t)cap * sizeof(int4)));
     BL_TRY(s->rep.ensure(al, N * sizeof(float2)));
     BL_TRY(s->walkcnt.ensure(al, 4 * sizeof(unsigned long long)));
     s->n = n;
@@ -1253,13 +1253,13 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st, cudaEv
                                                      s->nd_skip.as<int>(), s->lvl.as<int>());
     level_offsets_kernel<<<1, 32, 0, st>>>(s->lvl.as<int>());
     const int sms = device_sm_count();
-    level_bucket_kernel<<<sms * 4, 256, 0, st>>>(s->nd_level.as<int>(), s->cnt.as<int>(), n,
-                                                 s->lvl.as<int>(), s->lvl_nodes.as<int>());
+    level_bucket_kernel<<<sms * 4, 256, 0, st>>>(s->nd_level.as<int>(), s->nd_first.as<int>(),
+                                                 s->nd_count.as<int>(), s->nd_skip.as<int>(), s->cnt.as<int>(),
+                                                 n, s->lvl.as<int>(), s->lvl_info.as<int4>());
     for (int l = kLevels; l >= 0; l--)
         level_sums_kernel<<<std::min(div_up(n, 256), sms * 8), 256, 0, st>>>(
-            l, s->lvl.as<int>(), s->lvl_nodes.as<int>(), s->spos.as<float2>(), s->nd_first.as<int>(),
-            s->nd_count.as<int>(), s->nd_skip.as<int>(), s->box.as<float>(), s->nd_sum.as<float2>(),
-            s->nd_rec.as<float4>(), s->nd_aux.as<int2>());
+            l, s->lvl.as<int>(), s->lvl_info.as<int4>(), s->spos.as<float2>(), s->nd_skip.as<int>(),
+            s->box.as<float>(), s->nd_sum.as<float2>(), s->nd_rec.as<float4>(), s->nd_aux.as<int2>());
     BL_CUDA_TRY(cudaGetLastError());
     return BL_OK;
 }

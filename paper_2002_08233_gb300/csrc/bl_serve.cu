@@ -73,7 +73,9 @@ struct Job {
 size_t job_bytes(const Job& j) {
     const size_t n = (size_t)j.g->n;
     const size_t it = (size_t)j.iters;
-    if (j.mode == BL_BH) return 1100 * n + 16 * it + (4u << 20);
+    // Barnes-Hut: 17 n + 1 tree-node slots of 64 B (build fields, sums, walk
+    // records, level buckets) and ~110 B per vertex of sort, sweep and positions
+    if (j.mode == BL_BH) return 1200 * n + 16 * it + (4u << 20);
     if (j.small) return 8 * n + 8 * it + 4096;
     return 16 * n + 8 * it + (size_t)8 * 160 * j.chunk + 65536;
 }

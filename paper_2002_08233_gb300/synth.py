@@ -338,23 +338,42 @@ class Request:
     seed: int
 
 
-def serving_stream(count: int, rate_per_s: float, n_lo: int, n_hi: int,
-                   seed: int = 5) -> list[Request]:
-    """Poisson arrivals; sizes log-uniform in [n_lo, n_hi]; half R-MAT (edge
-    factor 8, folded into n vertices), half triangulated meshes."""
+def _stream_graph(args) -> CSR:
+    """Graph k of a serving stream: R-MAT (edge factor 8, folded into n vertices)
+    or a triangulated mesh of about n vertices, from its own seed."""
+    kind, n, gseed = args
+    if kind == 0:
+        scale = max(1, int(math.ceil(math.log2(n))))
+        return rmat(scale, 8, seed=gseed, n=n)
+    r = max(2, int(round(math.sqrt(n))))
+    return tri_mesh(r, max(2, int(round(n / r))), gseed)
+
+
+def serving_stream_plan(count: int, rate_per_s: float, n_lo: int, n_hi: int, seed: int = 5):
+    """Arrival times and each request's graph recipe (kind, n, graph seed)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=count)
     t = np.cumsum(gaps) - gaps[0]
     sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))
     kinds = rng.integers(0, 2, size=count)
-    out = []
-    for k in range(count):
-        n = int(round(sizes[k]))
-        if kinds[k] == 0:
-            scale = max(1, int(math.ceil(math.log2(n))))
-            g = rmat(scale, 8, seed=seed * 1000003 + k, n=n)
-        else:
-            r = max(2, int(round(math.sqrt(n))))
-            g = tri_mesh(r, max(2, int(round(n / r))), seed * 1000003 + k)
-        out.append(Request(arrival_s=float(t[k]), graph=g, seed=k))
-    return out
+    recipes = [(int(kinds[k]), int(round(sizes[k])), seed * 1000003 + k) for k in range(count)]
+    return [float(x) for x in t], recipes
+
+
+def serving_stream(count: int, rate_per_s: float, n_lo: int, n_hi: int,
+                   seed: int = 5, workers: int = 1):
+    """Poisson arrivals; sizes log-uniform in [n_lo, n_hi]; half R-MAT (edge
+    factor 8, folded into n vertices), half triangulated meshes. With workers > 1
+    the graphs are drawn by a pool of processes started with "spawn" (each graph
+    depends only on its own recipe, so the stream is the same) and the requests
+    are yielded in order as they are ready; otherwise a list is returned."""
+    times, recipes = serving_stream_plan(count, rate_per_s, n_lo, n_hi, seed)
+    if workers <= 1:
+        return [Request(arrival_s=times[k], graph=_stream_graph(recipes[k]), seed=k) for k in range(count)]
+
+    def gen():
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for k, g in enumerate(pool.imap(_stream_graph, recipes, chunksize=1)):
+                yield Request(arrival_s=times[k], graph=g, seed=k)
+    return gen()
