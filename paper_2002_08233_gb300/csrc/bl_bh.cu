@@ -73,6 +73,7 @@ struct BHState {
     DevBuf split, bigrows, midrows, old;   // row split points, long and medium rows, old attraction
     DevBuf corr;                        // float2[n]: exact repulsion of the CSR neighbours at S
     DevBuf lvl_ptr, tasks, seg_off, seg_sum;   // level-set schedule; segment partial sums
+    DevBuf scol;                        // earlier-minibatch columns of the rows of several segments
     DevBuf e_row, epart;                // per-row |ct|^2, reduction partials
     // the edge pass runs on a side stream while the tree is built and walked
     cudaStream_t side = nullptr;
@@ -91,7 +92,7 @@ void bh_state_free(BHState* s) {
                       &s->nd_level, &s->nd_skip, &s->nd_sum, &s->nd_rec, &s->nd_aux, &s->lvl,
                       &s->lvl_info, &s->rep, &s->walkcnt, &s->split, &s->bigrows, &s->midrows, &s->old,
                       &s->corr,
-                      &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->e_row,
+                      &s->lvl_ptr, &s->tasks, &s->seg_off, &s->seg_sum, &s->scol, &s->e_row,
                       &s->epart};
     for (DevBuf* b : bufs) b->release();
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
@@ -847,10 +848,16 @@ __global__ void __launch_bounds__(1024) edge_pass_big_kernel(
 // lower levels, and any order that runs a row after its earlier-minibatch
 // neighbours computes exactly the sequential minibatch sweep. Tasks are stored
 // level by level; a row with many earlier-minibatch edges is cut into segments
-// (tasks) and the last segment to finish combines the segment sums in order.
+// (tasks) whose partial sums segment 0's warp combines in a fixed order. Such a
+// row's earlier-minibatch columns are listed highest level first (`scol`), so
+// segment 0 holds the neighbours that finish last, and the later segments, which
+// need only lower levels, are scheduled at those levels: segment 0's warp waits
+// for its neighbours and, in the same polling loop, for the other segments'
+// partial sums, which are usually published long before.
 struct SweepArgs {
     const int* rowptr;
     const int* colids;
+    const int* scol;         // rows of several segments: their earlier-minibatch columns
     const float2* bold;      // positions at iteration start (S)
     float2* bnew;            // positions after this iteration's update
     const float2* rep;       // repulsion sums of the tree walk (unscaled)
@@ -941,11 +948,13 @@ __device__ __forceinline__ void task_prefetch_rec(const SweepArgs& a, int4 rec, 
     p.me = a.bold[i];
     p.rp = row_rep(a, i);
     p.od = a.old[i];
-    p.off = (p.tk.w >> 16) > 1 ? a.seg_off[i] : 0;
+    const bool multi = (p.tk.w >> 16) > 1;
+    p.off = multi ? a.seg_off[i] : 0;
+    const int* cols = multi ? a.scol : a.colids;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int e = p.tk.y + lane + 32 * k;
-        p.j[k] = e < p.tk.z ? __ldg(&a.colids[e]) : -1;
+        p.j[k] = e < p.tk.z ? __ldg(&cols[e]) : -1;
     }
 }
 
@@ -959,25 +968,29 @@ __global__ void level0_kernel(SweepArgs a) {
     }
 }
 
-// Dataflow sweep: no level barriers. Warps take the level-ordered tasks round
-// robin (task t goes to warp t mod warps), so every warp meets its tasks in level
-// order; a task reads each moved neighbour's slot until it is published. The
-// lowest-level unfinished task always has its inputs, because everything below
-// its level is finished or being finished by warps that are not waiting on it,
-// and all CTAs are resident (cooperative launch): the sweep cannot stall. Every
-// wait is bounded (BL_ETIMEOUT).
+// Dataflow sweep: no level barriers. Warps take the tasks round robin in list
+// order (task t goes to warp t mod warps); a task reads each moved neighbour's
+// slot (and segment 0 its row's partial-sum slots) until it is published. Every
+// task waits only for tasks earlier in the list, so the earliest unfinished task
+// has all its inputs and its warp has finished everything before it, and all CTAs
+// are resident (cooperative launch): the sweep cannot stall. Every wait is bounded
+// (BL_ETIMEOUT).
 struct Gather4 {
     int j[4];
     unsigned long long v[4];
 };
 
-// Reads the published positions of up to 4 ids per lane; false when the wait gave up.
-__device__ __forceinline__ bool gather_wait(const SweepArgs& a, Gather4& g, int lane) {
+// Reads the published positions of up to 4 ids per lane and, when `slot` is not
+// null, the lane's segment partial-sum slot into `sv`, until all are set; false
+// when the wait gave up.
+__device__ __forceinline__ bool gather_wait(const SweepArgs& a, Gather4& g, int lane,
+                                            const float2* slot, unsigned long long& sv) {
 #pragma unroll
     for (int k = 0; k < 4; k++) g.v[k] = g.j[k] >= 0 ? read_pos(&a.bnew[g.j[k]]) : 0ull;
+    if (slot != nullptr && sv == kUnset) sv = read_pos(slot);
     unsigned long long t0 = 0;
     for (unsigned spin = 0;; ++spin) {
-        bool pending = false;
+        bool pending = slot != nullptr && sv == kUnset;
 #pragma unroll
         for (int k = 0; k < 4; k++) pending |= g.j[k] >= 0 && g.v[k] == kUnset;
         if (!__any_sync(0xffffffffu, pending)) return true;
@@ -985,6 +998,7 @@ __device__ __forceinline__ bool gather_wait(const SweepArgs& a, Gather4& g, int 
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (g.j[k] >= 0 && g.v[k] == kUnset) g.v[k] = read_pos(&a.bnew[g.j[k]]);
+        if (slot != nullptr && sv == kUnset) sv = read_pos(slot);
         if ((spin & 127u) == 127u) {
             int bad = 0;
             if (lane == 0) {
@@ -1067,12 +1081,18 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
     if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t] = global_ns();
     const int seg = p.tk.w & 0xFFFF, nseg = p.tk.w >> 16;
     const float2 me = p.me;
+    const int* cols = nseg > 1 ? a.scol : a.colids;
+    // segment 0 of a row of at most 33 segments: lane l also waits for segment
+    // 1 + l's partial sum
+    const bool early = seg == 0 && nseg > 1 && nseg <= 33;
+    const float2* slot = early && 1 + lane < nseg ? &a.seg_sum[p.off + 1 + lane] : nullptr;
+    unsigned long long sv = kUnset;
     float sx = 0.f, sy = 0.f;
     Gather4 g;
 #pragma unroll
     for (int k = 0; k < 4; k++) g.j[k] = p.j[k];
     for (int e = p.tk.y + lane;;) {
-        if (!gather_wait(a, g, lane)) return false;
+        if (!gather_wait(a, g, lane, slot, sv)) return false;
         if (a.ttrace && lane == 0 && e == p.tk.y) a.ttrace[3 * (size_t)t + 1] = global_ns();
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -1080,12 +1100,24 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
         e += 128;
         if (!__any_sync(0xffffffffu, e < p.tk.z)) break;
 #pragma unroll
-        for (int k = 0; k < 4; k++) g.j[k] = e + 32 * k < p.tk.z ? __ldg(&a.colids[e + 32 * k]) : -1;
+        for (int k = 0; k < 4; k++) g.j[k] = e + 32 * k < p.tk.z ? __ldg(&cols[e + 32 * k]) : -1;
     }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
     if (nseg <= 1) {
         if (lane == 0) finish_row(a, i, me, p.rp, p.od, sx, sy);
+    } else if (early) {
+        // the same fixed order as seg_wait: lane 0 starts from segment 0's sum, lane
+        // l adds segment 1 + l, then the butterfly
+        float tx = lane == 0 ? sx : 0.f, ty = lane == 0 ? sy : 0.f;
+        if (slot != nullptr) {
+            const float2 w = unpack_pos(sv);
+            tx += w.x;
+            ty += w.y;
+        }
+        tx = warp_sum(tx);
+        ty = warp_sum(ty);
+        if (lane == 0) finish_row(a, i, me, p.rp, p.od, tx, ty);
     } else if (seg > 0) {
         // a later segment: its partial sum goes to its slot for segment 0's warp
         if (lane == 0) publish_partial(&a.seg_sum[p.off + seg], sx, sy);
@@ -1315,34 +1347,55 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
         level[i] = d + 1;
         nlev = std::max(nlev, d + 1);
     }
-    // tasks by level (rows in id order inside a level), big rows cut into segments
-    std::vector<int> lcount(nlev + 1, 0);
+    // Tasks. A row of at most segE earlier-minibatch edges is one task at the row's
+    // level. A longer row is cut into segments over its columns listed highest
+    // level first: segment 0 (the highest levels) stays at the row's level, and a
+    // later segment q, whose partial sum needs only its own columns, goes to level
+    // 1 + (the highest level among them), so it runs as soon as those columns are
+    // final rather than beside segment 0. Inside a level the later segments come
+    // first; every task then waits only for tasks before it in the list (the
+    // sweep's progress argument), rows in id order inside each group.
     std::vector<int> nseg(n);
     for (int i = 0; i < n; i++) {
         const int nd = split[i] - rp[i];
         nseg[i] = std::min(kMaxSeg, std::max(1, div_up(nd, segE)));   // longer segments past kMaxSeg
-        lcount[level[i]] += nseg[i];
     }
-    std::vector<int> lvl_ptr(nlev + 1, 0);   // levels 1..nlev -> slots 0..nlev-1
-    for (int l = 1; l <= nlev; l++) lvl_ptr[l] = lvl_ptr[l - 1] + lcount[l];
-    std::vector<int> fill(lvl_ptr.begin(), lvl_ptr.end() - 1);
-    std::vector<int4> tasks((size_t)lvl_ptr[nlev]);
+    std::vector<int4> recs;
+    std::vector<int> key;    // 2 (level - 1) + (0: later segment, 1: row or segment 0)
     std::vector<int> seg_off(n, 0);
+    std::vector<int> scol;   // rows of several segments: columns by level, highest first
     int nsegsum = 0;
     for (int i = 0; i < n; i++) {
         const int ns = nseg[i];
+        if (ns >= 65536) return set_error(BL_EINVAL, "Barnes-Hut sweep: row too long");
+        int e0 = rp[i], e1 = split[i];
         if (ns > 1) {
             seg_off[i] = nsegsum;
             nsegsum += ns;
+            const size_t base = scol.size();
+            scol.insert(scol.end(), ci + e0, ci + e1);
+            std::sort(scol.begin() + base, scol.end(), [&](int u, int v) {
+                return level[u] != level[v] ? level[u] > level[v] : u < v;
+            });
+            if (scol.size() > (size_t)0x7fffffff)
+                return set_error(BL_EINVAL, "Barnes-Hut sweep: too many edges in long rows");
+            e1 = (int)scol.size();
+            e0 = (int)base;
         }
-        const int e0 = rp[i], e1 = split[i];
         for (int q = 0; q < ns; q++) {
             const int a0 = e0 + (int)((int64_t)(e1 - e0) * q / ns);
             const int a1 = e0 + (int)((int64_t)(e1 - e0) * (q + 1) / ns);
-            tasks[fill[level[i] - 1]++] = make_int4(i, a0, a1, q | (ns << 16));
+            recs.push_back(make_int4(i, a0, a1, q | (ns << 16)));
+            key.push_back(q > 0 ? 2 * level[scol[a0]] : 2 * (level[i] - 1) + 1);
         }
-        if (ns >= 65536) return set_error(BL_EINVAL, "Barnes-Hut sweep: row too long");
     }
+    std::vector<int> kstart(2 * nlev + 1, 0);
+    for (int k : key) kstart[k + 1]++;
+    for (int k = 0; k < 2 * nlev; k++) kstart[k + 1] += kstart[k];
+    std::vector<int> lvl_ptr(nlev + 1, 0);   // levels 1..nlev -> slots 0..nlev-1
+    for (int l = 0; l <= nlev; l++) lvl_ptr[l] = kstart[2 * l];
+    std::vector<int4> tasks(recs.size());
+    for (size_t t = 0; t < recs.size(); t++) tasks[kstart[key[t]]++] = recs[t];
     const Allocator& al = L->alloc;
     auto up = [&](DevBuf& d, const void* h, size_t bytes) -> bl_status {
         BL_TRY(d.ensure(al, std::max<size_t>(bytes, 16)));
@@ -1355,6 +1408,7 @@ static bl_status bh_plan(bl_layout* L, int BS, cudaStream_t st) {
     BL_TRY(up(s->lvl_ptr, lvl_ptr.data(), lvl_ptr.size() * 4));
     BL_TRY(up(s->tasks, tasks.data(), tasks.size() * sizeof(int4)));
     BL_TRY(up(s->seg_off, seg_off.data(), seg_off.size() * 4));
+    BL_TRY(up(s->scol, scol.data(), scol.size() * 4));
     BL_TRY(s->seg_sum.ensure(al, (size_t)std::max(nsegsum, 1) * sizeof(float2)));
 
     BL_TRY(s->e_row.ensure(al, (size_t)n * 8));
@@ -1459,6 +1513,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
         SweepArgs a{};
         a.rowptr = L->g->rowptr.as<int>();
         a.colids = L->g->colids.as<int>();
+        a.scol = s->scol.as<int>();
         a.bold = S;
         a.bnew = bnew;
         a.rep = s->rep.as<float2>();
