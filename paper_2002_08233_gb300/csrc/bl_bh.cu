@@ -924,8 +924,8 @@ __device__ __forceinline__ void finish_row(const SweepArgs& a, int i, float2 me,
         nx = fmaf(sc, gx, me.x);
         ny = fmaf(sc, gy, me.y);
     }
+    publish_pos(&a.bnew[i], nx, ny);   // first: the rows waiting for it
     a.e_row[i] = (double)fmaf(fx, fx, fy * fy);
-    publish_pos(&a.bnew[i], nx, ny);
 }
 
 // Everything a task needs that the sweep does not change: the task record, the
