@@ -363,8 +363,10 @@ bl_status bl_debug_bh_counts(bl_layout *L, float theta, int32_t *far, int32_t *n
  * (any max_steps > 0) the last iteration's sweep is traced instead: the start
  * time of each of its dependency levels, then its end; with max_steps >= 2 these
  * are followed by three stamps per sweep task, in the sweep's task order (levels
- * in order, rows in id order within a level, long rows as consecutive segments):
- * {task start, its first earlier-minibatch positions gathered, task done}. */
+ * in order; inside a level first the later segments of long rows, each at the
+ * level after its own columns' highest, then the rows and first segments, each
+ * group in row id order): {task start, its first earlier-minibatch positions
+ * gathered, task done}. */
 bl_status bl_set_trace(bl_layout *L, int32_t max_steps);
 
 /* Phase timing of Barnes-Hut runs (profiling; the paper has no counterpart).
