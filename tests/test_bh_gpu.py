@@ -126,6 +126,33 @@ def test_bh_one_iteration_positions(core, name, maker, bs, seed):
     assert L.energy_history()[0] == pytest.approx(er[0], rel=1e-3)
 
 
+def _hubs_graph(n=40000, seed=21):
+    """ER background plus three hubs: vertex n-1 adjacent to every other vertex
+    (its earlier-minibatch columns fill the sweep's maximum of 257 segments, each
+    longer than one 128-column round), vertex n-300 to 5,000 random vertices (40
+    segments: partial sums read after the gather) and vertex 30,000 to 2,000 (16
+    segments: partial sums polled with the gather)."""
+    bg = synth.erdos_renyi(n, 4.0, seed)
+    rows = np.repeat(np.arange(n), np.diff(bg.rowptr.astype(np.int64)))
+    u, v = [rows], [bg.colids.astype(np.int64)]
+    rng = np.random.default_rng(seed)
+    u.append(np.full(n - 1, n - 1)); v.append(np.arange(n - 1))
+    u.append(np.full(5000, n - 300)); v.append(rng.choice(n - 300, 5000, replace=False))
+    u.append(np.full(2000, 30000)); v.append(rng.choice(30000, 2000, replace=False))
+    return synth.csr_from_edges(n, np.concatenate(u), np.concatenate(v), name="hubs40000")
+
+
+def test_bh_long_rows_positions(core):
+    """Rows of many sweep segments (the long-row paths of the sweep) against the
+    oracle's Algorithm S5 iteration."""
+    g = _hubs_graph()
+    xy = synth.uniform_positions(g.n, 4)
+    _, L = _layout(core, g, xy)
+    L.run(1, 256, "bh", 1.2)
+    xr, sens = oracle_sensitivity(g, xy, 1, 256, mode=oracle.BH, theta=1.2, nthreads=NCPU)
+    assert_positions("hubs40000", L.positions(), xr, TOL_POS_BH, sens)
+
+
 def test_bh_multi_iteration_continues(core):
     g = synth.erdos_renyi(3000, 5.0, 6)
     xy = synth.uniform_positions(g.n, 6)
