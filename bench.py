@@ -418,7 +418,7 @@ def run_bh(args, local, steps=5, warmup=2):
             d["achieved_gbs"] = pbytes[name] / (t_ms / 1e3) / 1e9
             d["frac_hbm"] = pbytes[name] / (t_ms / 1e3) / hbm
         phases[name] = d
-    phases["walk"]["node_record_bytes_l2"] = 24 * ph["walk_warp_visits"]
+    phases["walk"]["node_record_bytes_l1"] = 24 * ph["walk_node_visits"]
     achieved = tbytes / (ms_it / 1e3)
     # end to end through the public API: positions up, one iteration, positions down
     x0 = synth.uniform_positions(n, 0)

@@ -377,7 +377,8 @@ bl_status bl_set_trace(bl_layout *L, int32_t max_steps);
  * theta-walk, wait for the edge pass, minibatch sweep (first level + dataflow),
  * energy, edge pass (side stream, overlapping the tree and walk), whole
  * iteration}, out[9] = nodes of the last tree, out[10] = node records read by the
- * warps of the last walk, out[11] = iterations of that run (cap >= 12). */
+ * queries of the last walk (one per node a query visits), out[11] = iterations
+ * of that run (cap >= 12). */
 bl_status bl_set_phase_timing(bl_layout *L, int32_t on);
 bl_status bl_get_phase_times(const bl_layout *L, double *out, int64_t cap);
 

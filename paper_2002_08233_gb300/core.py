@@ -330,7 +330,7 @@ class Layout:
         out = np.zeros(12, dtype=np.float64)
         _check(_lib.bl_get_phase_times(self._h, _ptr(out), out.size))
         d = {k: float(out[q]) for q, k in enumerate(self.PHASES)}
-        d.update(nodes=int(out[9]), walk_warp_visits=int(out[10]), iterations=int(out[11]))
+        d.update(nodes=int(out[9]), walk_node_visits=int(out[10]), iterations=int(out[11]))
         return d
 
     def set_trace(self, max_steps: int):

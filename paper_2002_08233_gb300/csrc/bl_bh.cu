@@ -65,7 +65,7 @@ struct BHState {
     DevBuf lvl;                         // int[64]: per-level counts, offsets, fill
     DevBuf lvl_info;                    // nodes bucketed by level: int4 {node, first, count, skip}
     DevBuf rep;                         // float2[n]: repulsion sums (unscaled)
-    DevBuf walkcnt;                     // unsigned long long[3]: far nodes, near pairs, warp visits
+    DevBuf walkcnt;                     // unsigned long long[3]: far nodes, near pairs, node visits
     // sweep
     int plan_bs = -1, plan_seg = 0, nlevels = 0, nbig = 0, nmid = 0, lvl0_rows = 0;
     int64_t ntasks = 0;
@@ -589,7 +589,7 @@ __global__ void gather_sorted_kernel(const int* __restrict__ perm, const float2*
 }
 
 // ---------------------------------------------------------------------------
-// theta-walk (Algorithm S4), warp-cooperative; KAHAN: every term compensated
+// theta-walk (Algorithm S4), one query per lane; KAHAN: every term compensated
 // ---------------------------------------------------------------------------
 
 // s += v, compensated (Kahan) when KAHAN
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(256) walk_kernel(
     const float2 me = active ? spos[q] : make_float2(0.f, 0.f);
     float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
     unsigned next = active ? 0u : (unsigned)M;
-    unsigned far = 0, near = 0, visits = 0;   // visits: node records the warp read
+    unsigned far = 0, near = 0, visits = 0;   // visits: node records this lane read
     auto visit = [&](unsigned v) {
         const float4 rec = nd_rec[v];
         const int2 aux = nd_aux[v];
@@ -645,24 +645,28 @@ __global__ void __launch_bounds__(256) walk_kernel(
             }
         }
     };
-    for (;;) {
-        const unsigned v = __reduce_min_sync(0xffffffffu, next);
-        if (v >= (unsigned)M) break;
-        visits++;
-        if (next == v) visit(v);
+    // Every lane walks its own query's pre-order sequence at its own pace (the
+    // lanes of a warp are neighbouring queries, so they mostly read the same hot
+    // nodes, from L1); a lane's terms and their order are those of its own walk.
+    while (__any_sync(0xffffffffu, next < (unsigned)M)) {
+        if (next < (unsigned)M) {
+            visits++;
+            visit(next);
+        }
     }
     if (active) rep[i] = make_float2(sx - cx, sy - cy);
     if (active && qcounts != nullptr) qcounts[i] = make_int2((int)far, (int)near);   // parity hook
     // interaction counts for reporting
-    unsigned long long f = far, nr = near;
+    unsigned long long f = far, nr = near, vs = visits;
     for (int o = 16; o > 0; o >>= 1) {
         f += __shfl_xor_sync(0xffffffffu, f, o);
         nr += __shfl_xor_sync(0xffffffffu, nr, o);
+        vs += __shfl_xor_sync(0xffffffffu, vs, o);
     }
     if ((threadIdx.x & 31) == 0 && counts != nullptr) {
         atomicAdd(&counts[0], f);
         atomicAdd(&counts[1], nr);
-        atomicAdd(&counts[2], (unsigned long long)visits);
+        atomicAdd(&counts[2], vs);
     }
 }
 
