@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-also", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
-                    choices=["bh_rmat20", "grid32_600it", "batched_4096", "serving"],
+                    choices=["bh_rmat20", "grid32_600it", "batched_4096", "serving", "pair_ceiling"],
                     help="run one secondary workload alone and print its line (profiling)")
     ap.add_argument("--batched-count", type=int, default=4096, help="graphs of the batched line")
     ap.add_argument("--batched-iters", type=int, default=300, help="iterations of the batched line")
@@ -487,6 +487,22 @@ def cpu_baseline_bh(g, seconds_target=10.0):
 # secondary: the 32x32 grid (latency-bound), 600 iterations
 # ---------------------------------------------------------------------------
 
+def run_pair_ceiling(args, local):
+    """The exact pair loop and rcp.approx alone, against the SFU roofline's 16
+    reciprocal lanes per clock per SM (profiling line, not part of the default run)."""
+    from paper_2002_08233_gb300 import core
+    core.load()
+    core.use_torch()
+    shapes = {}
+    for threads, skip in ((512, False), (384, False), (512, True)):
+        r = core.measure_pair_rate(threads, skip)
+        r["frac_of_16"] = r["pairs_per_clk_per_sm"] / 16.0
+        shapes[f"{threads}_threads" + ("_sp0_idle" if skip else "")] = r
+    return {"workload": "one row per thread against a 256-column shared-memory tile, 400 passes, "
+                        "every SM; then 8 rcp.approx chains per thread, 512 threads per SM",
+            "pair_loop": shapes}
+
+
 def run_grid(args, local, reps=3):
     import torch
 
@@ -693,7 +709,7 @@ def main():
         return
     if args.only:
         fn = {"bh_rmat20": run_bh, "grid32_600it": run_grid, "batched_4096": run_batched,
-              "serving": run_serving}[args.only]
+              "serving": run_serving, "pair_ceiling": run_pair_ceiling}[args.only]
         line = fn(args, local)
         if rank == 0:
             print(json.dumps({"only": args.only, **line}))

@@ -89,6 +89,7 @@ def _declare(lib):
         "bl_set_trace": [P, i32],
         "bl_set_phase_timing": [P, i32],
         "bl_get_phase_times": [P, P, i64],
+        "bl_measure_pair_rate": [i32, i32, P, i64],
         "bl_get_trace": [P, P, i64, P],
         "bl_layout_run_noalloc": [i32, P, P, P, i32, i32, P, i64, P, P],
         "bl_layout_run_batch": [P, i32, i32, i32],
@@ -355,6 +356,14 @@ class Layout:
             self.close()
         except Exception:
             pass
+
+
+def measure_pair_rate(threads: int = 512, skip_sp0: bool = False) -> dict:
+    """Ceiling probes of the exact pair loop and of the SFU reciprocal (profiling)."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(load().bl_measure_pair_rate(int(threads), int(bool(skip_sp0)), _ptr(out), out.size))
+    return {"pairs_per_clk_per_sm": float(out[0]), "rcp_lanes_per_clk_per_sm": float(out[1]),
+            "pair_kernel_ms": float(out[2]), "sm_mhz_implied": float(out[3])}
 
 
 def greedy_layout(graph: Graph, v0: int = -1, seed: int = 0, K: float = 1.0, R: float = 1.0,

@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <vector>
 
 #include "bl_internal.cuh"
 
@@ -682,6 +683,118 @@ bl_status energy_reduce(const double* e_iter, int iters, int G, double* energy, 
     energy_reduce_kernel<<<div_up(iters, wpb), wpb * 32, 0, st>>>(e_iter, iters, G, energy);
     BL_CUDA_TRY(cudaGetLastError());
     return BL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ceiling probes: the pair loop and the SFU reciprocal alone (profiling)
+// ---------------------------------------------------------------------------
+
+// Every thread: one row against a 256-column tile in shared memory, `reps` times,
+// with the engine's pair loop (tile_pairs2). Warps on sub-partition 0 (w % 4 == 0)
+// sit out when skip_sp0. Lane 0 of each warp records its clock64 span.
+__global__ void __launch_bounds__(512, 1) pair_rate_kernel(const float4* __restrict__ src, int reps,
+                                                           int skip_sp0, float* out,
+                                                           long long* span) {
+    constexpr int NP = 128;
+    __shared__ float4 tile[NP];
+    for (int q = threadIdx.x; q < NP; q += blockDim.x) tile[q] = src[q];
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const float x = 0.001f * threadIdx.x, y = 0.002f * threadIdx.x + 0.5f;
+    f32x2 XI[1] = {pk2(x, x)}, YI[1] = {pk2(y, y)};
+    f32x2 AX[1] = {pk2(0.f, 0.f)}, AY[1] = {pk2(0.f, 0.f)};
+    const long long t0 = clock64();
+    if (!(skip_sp0 && w % 4 == 0))
+        for (int r = 0; r < reps; r++) tile_pairs2<1>(tile, NP, 0, 1, XI, YI, AX, AY);
+    const long long t1 = clock64();
+    float a, b, c, d;
+    upk2(AX[0], a, b);
+    upk2(AY[0], c, d);
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a + b + c + d;
+    if ((threadIdx.x & 31) == 0) span[blockIdx.x * 16 + w] = t1 - t0;
+}
+
+// Every thread: 8 independent chains of rcp.approx, `reps` rounds.
+__global__ void __launch_bounds__(512, 1) rcp_rate_kernel(int reps, float* out, long long* span) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = 1.5f + 0.01f * k + 1e-4f * threadIdx.x;
+    const long long t0 = clock64();
+    for (int r = 0; r < reps; r++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = rcp_sfu(v[k]);
+    }
+    const long long t1 = clock64();
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) sum += v[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+    if ((threadIdx.x & 31) == 0) span[blockIdx.x * 16 + (threadIdx.x >> 5)] = t1 - t0;
+}
+
+bl_status exact_pair_rate(int threads, int skip_sp0, double* pairs_per_clk, double* rcp_per_clk,
+                          double* pair_ms) {
+    if (threads < 32 || threads > 512 || threads % 32 != 0)
+        return set_error(BL_EINVAL, "pair-rate probe: threads a multiple of 32 in [32, 512]");
+    const int sms = device_sm_count();
+    cudaStream_t st = current_stream();
+    const Allocator& al = current_allocator();
+    DevBuf src, out, span;
+    BL_TRY(src.ensure(al, 128 * sizeof(float4)));
+    BL_TRY(out.ensure(al, (size_t)sms * 512 * sizeof(float)));
+    BL_TRY(span.ensure(al, (size_t)sms * 16 * sizeof(long long)));
+    float4 h[128];
+    for (int q = 0; q < 128; q++)
+        h[q] = make_float4(0.01f * q, 0.011f * q + 0.5f, 0.013f * q, 0.017f * q + 0.25f);
+    std::vector<long long> hs((size_t)sms * 16);
+    const int reps = 400;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bl_status s = BL_OK;
+    cudaError_t e = cudaMemcpyAsync(src.p, h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    auto max_span = [&](long long& m) {
+        e = cudaMemcpyAsync(hs.data(), span.p, hs.size() * sizeof(long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        m = 0;
+        for (long long v : hs) m = std::max(m, v);
+    };
+    const int warps = threads / 32;
+    const int active = skip_sp0 ? warps - (warps + 3) / 4 : warps;
+    long long m = 0;
+    for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {   // warm-up, then measured
+        if (e == cudaSuccess) e = cudaMemsetAsync(span.p, 0, hs.size() * sizeof(long long), st);
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) {
+            pair_rate_kernel<<<sms, threads, 0, st>>>(src.as<float4>(), reps, skip_sp0, out.as<float>(),
+                                                      span.as<long long>());
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) max_span(m);
+    }
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && m > 0) {
+        *pairs_per_clk = (double)active * 32 * 256.0 * reps / (double)m;
+        *pair_ms = ms;
+    }
+    for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {
+        e = cudaMemsetAsync(span.p, 0, hs.size() * sizeof(long long), st);
+        if (e == cudaSuccess) {
+            rcp_rate_kernel<<<sms, 512, 0, st>>>(2000, out.as<float>(), span.as<long long>());
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) max_span(m);
+    }
+    if (e == cudaSuccess && m > 0) *rcp_per_clk = 512.0 * 8 * 2000 / (double)m;
+    if (e != cudaSuccess) s = cuda_error(e, "pair-rate probe");
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    src.release();
+    out.release();
+    span.release();
+    return s;
 }
 
 // ---------------------------------------------------------------------------

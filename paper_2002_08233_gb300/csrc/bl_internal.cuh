@@ -175,6 +175,10 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
 bl_status exact_launch(const ExactPlan& plan, const ExactTask& task, const ExactParams& prm,
                        cudaStream_t st);
 
+// Ceiling probes of the pair loop and of rcp.approx (bl_measure_pair_rate).
+bl_status exact_pair_rate(int threads, int skip_sp0, double* pairs_per_clk, double* rcp_per_clk,
+                          double* pair_ms);
+
 // Status word, grid-barrier counter and their reset (bl_runtime.cu).
 bl_status layout_reset_sync_words(bl_layout* L, cudaStream_t st);
 unsigned* layout_barrier_word(bl_layout* L);

@@ -672,6 +672,20 @@ bl_status bl_set_phase_timing(bl_layout* L, int32_t on) {
     return BL_OK;
 }
 
+bl_status bl_measure_pair_rate(int32_t threads, int32_t skip_sp0, double* out, int64_t cap) {
+    if (!out || cap < 4) return set_error(BL_EINVAL, "bl_measure_pair_rate: output needs 4 doubles");
+    double ppc = 0.0, rpc = 0.0, ms = 0.0;
+    BL_TRY(exact_pair_rate(threads, skip_sp0, &ppc, &rpc, &ms));
+    const int warps = threads / 32;
+    const double active = skip_sp0 ? warps - (warps + 3) / 4 : warps;
+    const double pairs = (double)device_sm_count() * active * 32 * 256.0 * 400;
+    out[0] = ppc;
+    out[1] = rpc;
+    out[2] = ms;
+    out[3] = ms > 0 && ppc > 0 ? pairs / (ms * 1e-3) / (ppc * device_sm_count()) / 1e6 : 0.0;
+    return BL_OK;
+}
+
 bl_status bl_get_phase_times(const bl_layout* L, double* out, int64_t cap) {
     if (!L || !out) return set_error(BL_EINVAL, "bl_get_phase_times: NULL argument");
     if (cap < kPhaseSlots + 3) return set_error(BL_EINVAL, "bl_get_phase_times: output needs 12 doubles");

@@ -257,3 +257,16 @@ def test_split_runs_equal_one_run(core, engine, n, bs):
         e.extend(P.energy_history().tolist())
     assert np.array_equal(A.positions(), P.positions())
     assert np.array_equal(A.energy_history(), np.array(e))
+
+
+def test_pair_rate_probe(core):
+    """The ceiling probe measures the pair loop below the SFU's 16 reciprocal lanes
+    per clock per SM (one reciprocal per pair) and the reciprocal alone near them."""
+    r = core.measure_pair_rate(512)
+    assert 4.0 < r["pairs_per_clk_per_sm"] <= 16.5, r
+    assert 8.0 < r["rcp_lanes_per_clk_per_sm"] <= 33.0, r
+    assert r["pair_kernel_ms"] > 0 and 500 < r["sm_mhz_implied"] < 2500, r
+    idle = core.measure_pair_rate(512, skip_sp0=True)
+    assert 0 < idle["pairs_per_clk_per_sm"] <= 16.5, idle
+    with pytest.raises(core.BatchLayoutError):
+        core.measure_pair_rate(100)
