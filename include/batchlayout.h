@@ -386,10 +386,11 @@ bl_status bl_set_phase_timing(bl_layout *L, int32_t on);
  * run one row against a 256-column tile in shared memory with the exact engine's
  * packed pair loop, 400 times; with skip_sp0 != 0 the warps of sub-partition 0
  * (warp index % 4 == 0) sit out. Then 512 threads per SM run 8 independent chains
- * of rcp.approx. out[0] = pair interactions per clock per SM (longest warp's
- * clock64 span), out[1] = reciprocal lanes per clock per SM, out[2] = the pair
- * kernel's device milliseconds (CUDA events), out[3] = the SM clock those imply
- * (MHz). cap >= 4. Allocates and frees its scratch; synchronises. */
+ * of rcp.approx(x/2 + 1). out[0] = pair interactions per clock per SM (longest warp's
+ * clock64 span), out[1] = reciprocal lanes per clock per SM (CUDA events, at the
+ * clock of out[3]), out[2] = the pair kernel's device milliseconds (CUDA events),
+ * out[3] = the SM clock those imply (MHz). cap >= 4. Allocates and frees its
+ * scratch; synchronises. */
 bl_status bl_measure_pair_rate(int32_t threads, int32_t skip_sp0, double *out, int64_t cap);
 bl_status bl_get_phase_times(const bl_layout *L, double *out, int64_t cap);
 

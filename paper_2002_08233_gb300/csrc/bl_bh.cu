@@ -549,6 +549,11 @@ __global__ void level_sums_kernel(int l, const int* __restrict__ lvl, const int4
                                   const float2* __restrict__ spos, const int* __restrict__ nd_skip,
                                   const float* __restrict__ box, float2* __restrict__ nd_sum,
                                   float4* __restrict__ nd_rec, int2* __restrict__ nd_aux) {
+    // Programmatic dependent launch: the next level's grid may be scheduled now, and
+    // this grid reads nothing before the previous level's grid has completed and its
+    // writes are visible.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lo = lvl[20 + l], hi = lvl[20 + l + 1];
     const float Dl2 = box[4 + l];
     for (int q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) {
@@ -1292,10 +1297,22 @@ static bl_status bh_build(bl_layout* L, const float2* S, cudaStream_t st, cudaEv
     level_bucket_kernel<<<sms * 4, 256, 0, st>>>(s->nd_level.as<int>(), s->nd_first.as<int>(),
                                                  s->nd_count.as<int>(), s->nd_skip.as<int>(), s->cnt.as<int>(),
                                                  n, s->lvl.as<int>(), s->lvl_info.as<int4>());
+    // bottom-up, one launch per level; each launch may start while the previous one
+    // drains (programmatic dependent launch), and waits inside for its completion
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::min(div_up(n, 256), sms * 8));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     for (int l = kLevels; l >= 0; l--)
-        level_sums_kernel<<<std::min(div_up(n, 256), sms * 8), 256, 0, st>>>(
-            l, s->lvl.as<int>(), s->lvl_info.as<int4>(), s->spos.as<float2>(), s->nd_skip.as<int>(),
-            s->box.as<float>(), s->nd_sum.as<float2>(), s->nd_rec.as<float4>(), s->nd_aux.as<int2>());
+        BL_CUDA_TRY(cudaLaunchKernelEx(&cfg, level_sums_kernel, l, (const int*)s->lvl.as<int>(),
+                                       (const int4*)s->lvl_info.as<int4>(), (const float2*)s->spos.as<float2>(),
+                                       (const int*)s->nd_skip.as<int>(), (const float*)s->box.as<float>(),
+                                       s->nd_sum.as<float2>(), s->nd_rec.as<float4>(), s->nd_aux.as<int2>()));
     BL_CUDA_TRY(cudaGetLastError());
     return BL_OK;
 }

@@ -714,22 +714,20 @@ __global__ void __launch_bounds__(512, 1) pair_rate_kernel(const float4* __restr
     if ((threadIdx.x & 31) == 0) span[blockIdx.x * 16 + w] = t1 - t0;
 }
 
-// Every thread: 8 independent chains of rcp.approx, `reps` rounds.
-__global__ void __launch_bounds__(512, 1) rcp_rate_kernel(int reps, float* out, long long* span) {
+// Every thread: 8 independent chains x <- rcp.approx(x/2 + 1), `reps` rounds (timed with
+// CUDA events: the clock of the SM is read at issue, ahead of the chains' results).
+__global__ void __launch_bounds__(512, 1) rcp_rate_kernel(int reps, float* out) {
     float v[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) v[k] = 1.5f + 0.01f * k + 1e-4f * threadIdx.x;
-    const long long t0 = clock64();
     for (int r = 0; r < reps; r++) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = rcp_sfu(v[k]);
+        for (int k = 0; k < 8; k++) v[k] = rcp_sfu(fmaf(v[k], 0.5f, 1.0f));   // no rcp(rcp(x)) to fold
     }
-    const long long t1 = clock64();
     float sum = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; k++) sum += v[k];
     out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
-    if ((threadIdx.x & 31) == 0) span[blockIdx.x * 16 + (threadIdx.x >> 5)] = t1 - t0;
 }
 
 bl_status exact_pair_rate(int threads, int skip_sp0, double* pairs_per_clk, double* rcp_per_clk,
@@ -779,15 +777,22 @@ bl_status exact_pair_rate(int threads, int skip_sp0, double* pairs_per_clk, doub
         *pairs_per_clk = (double)active * 32 * 256.0 * reps / (double)m;
         *pair_ms = ms;
     }
+    // SM clock of the pair kernel (its spans against its events), for the reciprocals
+    const double mhz = (e == cudaSuccess && ms > 0 && m > 0) ? (double)m / (ms * 1e3) : 0.0;
+    const int rreps = 20000;
     for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {
-        e = cudaMemsetAsync(span.p, 0, hs.size() * sizeof(long long), st);
+        e = cudaEventRecord(a, st);
         if (e == cudaSuccess) {
-            rcp_rate_kernel<<<sms, 512, 0, st>>>(2000, out.as<float>(), span.as<long long>());
+            rcp_rate_kernel<<<sms, 512, 0, st>>>(rreps, out.as<float>());
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) max_span(m);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
     }
-    if (e == cudaSuccess && m > 0) *rcp_per_clk = 512.0 * 8 * 2000 / (double)m;
+    float rms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&rms, a, b);
+    if (e == cudaSuccess && rms > 0 && mhz > 0)
+        *rcp_per_clk = 512.0 * 8 * rreps / ((double)rms * 1e3 * mhz);
     if (e != cudaSuccess) s = cuda_error(e, "pair-rate probe");
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
