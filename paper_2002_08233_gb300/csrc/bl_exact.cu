@@ -97,6 +97,12 @@ __device__ __forceinline__ void tile_pairs2(const float4* __restrict__ tile, int
 // warp-uniform range [mlo, mhi) covering every m flagged in need[] by any lane
 template <int RPT>
 __device__ __forceinline__ void need_range(const bool (&need)[RPT], int& mlo, int& mhi) {
+    if (RPT == 1) {   // one vote
+        const bool any = __any_sync(0xffffffffu, need[0]);
+        mlo = any ? 0 : 1;
+        mhi = any ? 1 : 0;
+        return;
+    }
     int lo = RPT, hi = 0;
 #pragma unroll
     for (int m = 0; m < RPT; m++)
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                                          : wb - (wb + 1) / 4;
     f32x2 XI[RPT], YI[RPT];
     float sx[RPT], sy[RPT], cx[RPT], cy[RPT];
-    int bi[RPT], lrow[RPT];
+    int bi[RPT], lrow[RPT], cslot[RPT];   // batch, local row, slot among its batch's critical rows
 #pragma unroll
     for (int m = 0; m < RPT; m++) {
         const int li = lane + 32 * (wslot + NW * m);
@@ -216,6 +222,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
         bi[m] = v ? i / BS : -1;
         lrow[m] = li;
+        int lo = 0, hi = 0;
+        if (v) crit_range(bi[m], BS, n, rank, G, lo, hi);
+        cslot[m] = li - lo;
     }
     for (int li = tid; li < nloc; li += T) {
         const int i = rank + G * li;
@@ -308,15 +317,13 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         __syncthreads();
     }
 
-    // bulk: post the sums of the rows of batch kk into crep and restart them
+    // bulk: post the sums of the rows of batch kk into crep and restart them (the
+    // slot of a row among its batch's critical rows is fixed: cslot, set above)
     auto post_rows = [&](int kk, float2* crep) {
-        int lo, hi;
-        crit_range(kk, BS, n, rank, G, lo, hi);
 #pragma unroll
         for (int m = 0; m < RPT; m++) {
-            const int li = lrow[m];
-            if (bi[m] == kk && li >= lo && li < hi) {
-                crep[li - lo] = make_float2(sx[m] - cx[m], sy[m] - cy[m]);
+            if (bi[m] == kk) {
+                crep[cslot[m]] = make_float2(sx[m] - cx[m], sy[m] - cy[m]);
                 sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
             }
         }
