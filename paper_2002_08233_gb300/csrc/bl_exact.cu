@@ -75,7 +75,7 @@ __device__ __forceinline__ void tile_pairs2(const float4* __restrict__ tile, int
         asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(AY[m]) : "l"(dy), "l"(inv));
     };
     if (mlo == 0 && mhi == RPT) {   // every row: no predicate in the loop
-#pragma unroll 8
+#pragma unroll 16
         for (int q = 0; q < np; q++) {
             const float4 p = tile[q];
             const f32x2 X = pk2(p.x, p.y), Y = pk2(p.z, p.w);
@@ -640,14 +640,18 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (s_ctl[0]) return;
             if (tb == 0) trace_mark(tk, rank, s, 7);
             const float4* tile = s_tile + (size_t)(s & 1) * TQ;
-            // rows moved at step s-1 by the control warp
+            // rows moved at step s-1 by the control warp (every lane reads, so that
+            // the warp does not diverge; a row's own slot, or slot 0 for a lane
+            // without a row)
 #pragma unroll
-            for (int m = 0; m < RPT; m++)
-                if (s > 0 && bi[m] == kprev) {
-                    const float2 p = s_pos[lrow[m]];
+            for (int m = 0; m < RPT; m++) {
+                const bool moved = s > 0 && bi[m] == kprev;
+                const float2 p = s_pos[bi[m] >= 0 ? lrow[m] : 0];
+                if (moved) {
                     XI[m] = pk2(p.x, p.x);
                     YI[m] = pk2(p.y, p.y);
                 }
+            }
             if (tb == 0) trace_mark(tk, rank, s, 5);
             if (is_stager && s + 1 < S) {   // neighbours of step s+1, ids of step s+2
                 const int kn = (k + 1) % B;
