@@ -116,7 +116,7 @@ __device__ __forceinline__ void need_range(const bool (&need)[RPT], int& mlo, in
 
 // Shared-memory carve-up (bytes); the host sizes the launch with the same code.
 struct EngineSmem {
-    int tile, pos, rpl, rpe, crep, off, cid, nbr, ctl, total;
+    int tile, pos, rpl, rpe, crep, off, cid, nbr, pre, prel, ctl, total;
     __host__ __device__ EngineSmem(int BS, int nloc, int CR, int CAP, int NW) {
         const int TQ = (BS + 1) / 2;
         tile = 0;                                        // 2 x TQ float4: column tiles
@@ -127,7 +127,9 @@ struct EngineSmem {
         off = crep + ((2 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
         cid = off + ((3 * (CR + 1) * 4 + 15) / 16) * 16; // 3 x CAP int: staged column ids
         nbr = cid + 3 * CAP * 4;                         // 2 x CAP float2: staged positions
-        ctl = nbr + 2 * CAP * 8;                         // control words
+        pre = nbr + 2 * CAP * 8;                         // 2 x CR float4: CSR sums without the last batch
+        prel = pre + 2 * CR * 16;                        // 2 x CR int: edges into the last batch
+        ctl = prel + ((2 * CR * 4 + 15) / 16) * 16;      // control words
         total = ctl + 64;
     }
 };
@@ -154,6 +156,7 @@ __device__ __forceinline__ void bar_arrive_n(int id, int count) {
 }
 constexpr int kBarTile = 1;   // control warp -> bulk warps: tile of step s ready
 constexpr int kBarDone = 2;   // bulk warps -> control warp: step s finished
+constexpr int kBarPre = 3;    // staging warp -> control warp: CSR sums of step s+1 ready
 constexpr int kCritLanes = 4; // critical rows the control warp finishes together
 
 // phase timestamp (global timer, ns) of step s, slot q, when tracing
@@ -187,6 +190,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     int* s_off = reinterpret_cast<int*>(smem + L.off);
     int* s_cid = reinterpret_cast<int*>(smem + L.cid);
     float2* s_nbr = reinterpret_cast<float2*>(smem + L.nbr);
+    float4* s_pre = reinterpret_cast<float4*>(smem + L.pre);
+    int* s_prel = reinterpret_cast<int*>(smem + L.prel);
     volatile int* s_ctl = reinterpret_cast<volatile int*>(smem + L.ctl);
 
     const int tid = threadIdx.x, lane = tid & 31;
@@ -373,6 +378,48 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         }
         cp_async_commit();
     };
+    // The staging warp, once the positions of step s+1 have landed: the CSR sums of
+    // batch kk's rows over every neighbour except those in batch kl (the batch the
+    // control warp moves at step s, whose positions only the tile of step s+1 has),
+    // one row at a time over the whole warp (lanes over the edges in order, then a
+    // butterfly), into s_pre[pslot]; s_prel counts each row's edges into batch kl,
+    // whose terms the control warp adds at step s+1.
+    auto csr_pre = [&](int kk, int kl, int slot, int pslot, const float2* bnew, const float2* bold) {
+        int lo, hi;
+        crit_range(kk, BS, n, rank, G, lo, hi);
+        const int* off = s_off + slot * (CR + 1);
+        const int* cid = s_cid + (size_t)slot * CAP;
+        const float2* nbr = s_nbr + (size_t)pslot * CAP;
+        const int kllo = kl * BS, kln = min(BS, n - kllo);
+        for (int c = 0; c < hi - lo; c++) {
+            const int li = lo + c;
+            const int e0 = s_rpl[li], e1 = s_rpe[li];
+            const float2 me = s_pos[li];
+            float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
+            int late = 0;
+            for (int ee = e0 + lane; ee < e1; ee += 32) {
+                const int f = off[c] + (ee - e0);
+                const int j = f < CAP ? cid[f] : __ldg(&tk.colids[ee]);
+                if ((unsigned)(j - kllo) < (unsigned)kln) {
+                    late++;
+                    continue;
+                }
+                const float2 pj = f < CAP ? nbr[f] : __ldcg(j < kk * BS ? bnew + j : bold + j);
+                edge_terms(me.x, me.y, pj, invK, am, rn, ax, ay, qx, qy);
+            }
+            ax = warp_sum(ax);
+            ay = warp_sum(ay);
+            qx = warp_sum(qx);
+            qy = warp_sum(qy);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) late += __shfl_xor_sync(0xffffffffu, late, o);
+            if (lane == 0) {
+                s_pre[pslot * CR + c] = make_float4(ax, ay, qx, qy);
+                s_prel[pslot * CR + c] = late;
+            }
+        }
+        __syncwarp();
+    };
 
     // ---- control warp: finish the rows of batch k --------------------------------------
     // Rows kCritLanes at a time. Column kprev: 8 lanes per row over the tile, then a
@@ -382,7 +429,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     int cur_s = 0;   // step being traced (control warp)
     auto ctl_critical = [&](int k, int kprev, int slot, int pslot, const float4* tile,
                             float stepf, const float2* bnew, const float2* bold,
-                            const float2* crep, float2* out) -> double {
+                            const float2* crep, float2* out, bool pre_ok) -> double {
         int lo, hi;
         crit_range(k, BS, n, rank, G, lo, hi);
         const int* off = s_off + slot * (CR + 1);
@@ -399,6 +446,8 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             return __ldcg(j < k * BS ? bnew + j : bold + j);
         };
         double e = 0.0;
+        // the staging warp's CSR sums of this step (once per step, rows or not)
+        if (pre_ok && !snapshot && cur_s > 0) bar_sync_n(kBarPre, 64);
         for (int c0 = 0; c0 < hi - lo; c0 += kCritLanes) {
             const int nr = min(kCritLanes, hi - lo - c0);
             // column kprev: lane group g = lane / 8 takes row c0 + g
@@ -420,9 +469,37 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 ry += __shfl_xor_sync(0xffffffffu, ry, o);
             }
             if (lane == 0 && c0 == 0 && !snapshot) trace_mark(tk, rank, cur_s, 9);
-            // hub rows: whole-warp CSR sums
+            // with the staging warp's sums (pre_ok): each row's sum without batch kprev,
+            // plus, when it has edges into kprev, their terms from the tile (whole warp)
             float hax = 0.f, hay = 0.f, hqx = 0.f, hqy = 0.f;
-            for (int r = 0; r < nr; r++) {
+            if (pre_ok) {
+                for (int r = 0; r < nr; r++) {
+                    const int c = c0 + r;
+                    float4 v = s_pre[pslot * CR + c];
+                    if (s_prel[pslot * CR + c] > 0) {   // warp-uniform
+                        const int li = lo + c;
+                        const int e0 = s_rpl[li], e1 = s_rpe[li];
+                        const float2 me = s_pos[li];
+                        float lx = 0.f, ly = 0.f, lqx = 0.f, lqy = 0.f;
+                        for (int ee = e0 + lane; ee < e1; ee += 32) {
+                            const int f = off[c] + (ee - e0);
+                            const int j = f < CAP ? cid[f] : __ldg(&tk.colids[ee]);
+                            const unsigned o = (unsigned)(j - kplo);
+                            if (o < (unsigned)kpn)
+                                edge_terms(me.x, me.y, tile_col(tile, (int)o), invK, am, rn, lx, ly, lqx, lqy);
+                        }
+                        v.x += warp_sum(lx);
+                        v.y += warp_sum(ly);
+                        v.z += warp_sum(lqx);
+                        v.w += warp_sum(lqy);
+                    }
+                    if (lane == r) {
+                        hax = v.x; hay = v.y; hqx = v.z; hqy = v.w;
+                    }
+                }
+            }
+            // hub rows: whole-warp CSR sums
+            for (int r = 0; r < nr && !pre_ok; r++) {
                 const int li = lo + c0 + r;
                 const int e0 = s_rpl[li], e1 = s_rpe[li];
                 if (e1 - e0 <= 32) continue;   // warp-uniform
@@ -440,7 +517,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             }
             // rows with at most 32 edges: the row's W lanes split its edges
             float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f;
-            if (g < nr) {
+            if (g < nr && !pre_ok) {
                 const int li = lo + c0 + g;
                 const int e0 = s_rpl[li], e1 = s_rpe[li];
                 if (e1 - e0 <= 32) {
@@ -468,7 +545,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 const int i = rank + G * li;
                 const float2 me = s_pos[li];
                 const int e0 = s_rpl[li], e1 = s_rpe[li];
-                if (e1 - e0 > 32) {
+                if (pre_ok || e1 - e0 > 32) {   // sums held by lane g
                     ax = hax_g; ay = hay_g; qx = hqx_g; qy = hqy_g;
                 }
                 float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
@@ -521,7 +598,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 __syncwarp();
             }
             __syncthreads();
-            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out);
+            if (is_ctl) ctl_critical(k, -1, 0, 0, s_tile, 0.f, buf0, buf0, s_crep, tk.f_out, false);
             __syncthreads();
         }
         return;
@@ -539,6 +616,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         stage_pos(0, -1, 0, 0, buf1, buf0);
         cp_async_wait_all();
         __syncwarp();
+        // step 0 takes batch B-1 from its tile (the start positions), like every step
+        // its previous batch, so that a launch's first step sums as a continuing one
+        csr_pre(0, B - 1, 0, 0, buf1, buf0);
     }
     __syncthreads();
 
@@ -615,7 +695,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (lane == 0) trace_mark(tk, rank, s, 3);
             bar_arrive_n(kBarTile, T);            // bulk may start step s
             const double e = ctl_critical(k, kprev, s % 3, s & 1, tile, (float)step, bnew, bold,
-                                          s_crep + (size_t)(s & 1) * CR, bnew);
+                                          s_crep + (size_t)(s & 1) * CR, bnew, true);
             if (lane == 0) trace_mark(tk, rank, s, 4);
             e_iter += e;
             __syncwarp();
@@ -656,8 +736,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (is_stager && s + 1 < S) {   // neighbours of step s+1, ids of step s+2
                 const int kn = (k + 1) % B;
                 const int itn = kn == 0 ? it + 1 : it;
-                stage_pos(kn, k, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1,
-                          (itn & 1) ? buf1 : buf0);
+                const float2* nb = (itn & 1) ? buf0 : buf1;
+                const float2* ob = (itn & 1) ? buf1 : buf0;
+                stage_pos(kn, k, (s + 1) % 3, (s + 1) & 1, nb, ob);
                 if (s + 2 < S) stage_ids((k + 2) % B, (s + 2) % 3);
             }
             const bool last_iter = (it + 1 == tk.iters);
@@ -668,9 +749,19 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (tb == 0) trace_mark(tk, rank, s, 10);
             add_tile(tile, kpn, need);
             post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * CR);
-            if (is_stager) cp_async_wait_all();   // staged data lands before "done"
             if (tb == 0) trace_mark(tk, rank, s, 8);
             bar_arrive_n(kBarDone, T);
+            // the staging warp: once the positions of step s+1 have landed, that step's
+            // CSR sums, announced to the control warp on their own barrier (the control
+            // warp reads neither the staged positions nor these sums before then)
+            if (is_stager && s + 1 < S) {
+                const int kn = (k + 1) % B;
+                const int itn = kn == 0 ? it + 1 : it;
+                cp_async_wait_all();
+                __syncwarp();
+                csr_pre(kn, k, (s + 1) % 3, (s + 1) & 1, (itn & 1) ? buf0 : buf1, (itn & 1) ? buf1 : buf0);
+                bar_arrive_n(kBarPre, 64);
+            }
         }
     }
 }
