@@ -123,8 +123,8 @@ struct EngineSmem {
         pos = tile + 2 * TQ * 16;                        // nloc float2: local positions
         rpl = pos + ((nloc * 8 + 15) / 16) * 16;         // nloc int: rowptr[i]
         rpe = rpl + ((nloc * 4 + 15) / 16) * 16;         // nloc int: rowptr[i+1]
-        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 x CR float2: critical sums
-        off = crep + ((2 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
+        crep = rpe + ((nloc * 4 + 15) / 16) * 16;        // 2 steps x 2 halves x CR float2: bulk sums
+        off = crep + ((4 * CR * 8 + 15) / 16) * 16;      // 3 x (CR+1) int: edge offsets
         cid = off + ((3 * (CR + 1) * 4 + 15) / 16) * 16; // 3 x CAP int: staged column ids
         nbr = cid + 3 * CAP * 4;                         // 2 x CAP float2: staged positions
         pre = nbr + 2 * CAP * 8;                         // 2 x CR float4: CSR sums without the last batch
@@ -208,23 +208,35 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     float2* const buf1 = tk.pos_alt;
 
     // ---- bulk state: blocks of 32 consecutive local rows per warp (so a warp's rows
-    //      share few minibatches and whole warps skip columns they do not need);
-    //      blocks go first to the warps that do not share a sub-partition with the
-    //      control warp (hardware warp w runs on sub-partition w % 4) -------------------
+    //      share few minibatches and whole warps skip columns they do not need).
+    //      One row per thread: every row's repulsion is kept as two sums, over the
+    //      first and the second half of every column tile, and a warp's piece (set by
+    //      the host) is a whole block (both halves), one half of a block, or a block
+    //      of at most 16 rows folded onto the warp (lanes 0-15 the first half, lanes
+    //      16-31 the second), so that the pieces spread the work evenly over the four
+    //      sub-partitions (hardware warp w runs on sub-partition w % 4), the control
+    //      warp's getting less. Several rows per thread: a block per warp and turn,
+    //      the control warp's sub-partition served last, one sum per row. -----------------
     const int wslot = (wb + 1) % 4 == 0 ? (NW - NW / 4) + (wb + 1) / 4 - 1
                                          : wb - (wb + 1) / 4;
+    const int pcode = RPT == 1 && !is_ctl ? tk.piece[wb] : 0;
+    const bool pfold = (pcode >> 18) & 1;
+    // halves this thread sums for its row (bit 0: first, bit 1: second)
+    const int hm = RPT > 1 ? 1 : (pfold ? (lane < 16 ? 1 : 2) : ((pcode >> 16) & 3));
     f32x2 XI[RPT], YI[RPT];
-    float sx[RPT], sy[RPT], cx[RPT], cy[RPT];
+    float sx[2][RPT], sy[2][RPT], cx[2][RPT], cy[2][RPT];
     int bi[RPT], lrow[RPT], cslot[RPT];   // batch, local row, slot among its batch's critical rows
 #pragma unroll
     for (int m = 0; m < RPT; m++) {
-        const int li = lane + 32 * (wslot + NW * m);
-        const bool v = !is_ctl && li < nloc;
+        const int li = RPT == 1 ? 32 * (pcode & 0xFFFF) + (pfold ? (lane & 15) : lane)
+                                : lane + 32 * (wslot + NW * m);
+        const bool v = !is_ctl && hm != 0 && li < nloc;
         const int i = rank + G * li;
         const float2 p = v ? __ldcg(&buf0[i]) : make_float2(0.f, 0.f);
         XI[m] = pk2(p.x, p.x);
         YI[m] = pk2(p.y, p.y);
-        sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) sx[h][m] = sy[h][m] = cx[h][m] = cy[h][m] = 0.f;
         bi[m] = v ? i / BS : -1;
         lrow[m] = li;
         int lo = 0, hi = 0;
@@ -239,34 +251,94 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
     }
     if (tid == 0) s_ctl[0] = 0;
 
+    // s += v into a row's sum (compensated across tiles when kahan)
+    auto acc = [&](float& sum, float& comp, float v) {
+        if (kahan)
+            kahan_add(sum, comp, v);
+        else
+            sum += v;
+    };
     // pair loop + tail + Kahan for the flagged rows against a paired tile of nc columns
     auto add_tile = [&](const float4* tile, int nc, const bool (&need)[RPT]) {
-        int mlo, mhi;
-        need_range<RPT>(need, mlo, mhi);
-        if (mlo >= mhi) return;
-        f32x2 AX[RPT], AY[RPT];
-#pragma unroll
-        for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
-        tile_pairs2<RPT>(tile, nc >> 1, mlo, mhi, XI, YI, AX, AY);
-#pragma unroll
-        for (int m = 0; m < RPT; m++) {
-            float a0, a1, b0, b1, xi, yi, dummy;
-            upk2(AX[m], a0, a1);
-            upk2(AY[m], b0, b1);
-            upk2(XI[m], xi, dummy);
-            upk2(YI[m], yi, dummy);
-            float ax = a0 + a1, ay = b0 + b1;
-            if (nc & 1) {
-                const float2 pc = tile_col(tile, nc - 1);
-                rep_pair(xi, yi, pc.x, pc.y, ax, ay);
-            }
-            if (need[m]) {
-                if (kahan) {   // compensated across the row's column tiles
-                    kahan_add(sx[m], cx[m], ax);
-                    kahan_add(sy[m], cy[m], ay);
+        if constexpr (RPT == 1) {
+            // half 0: column pairs [0, hp); half 1: [hp, np) and an odd last column
+            if (!__any_sync(0xffffffffu, need[0])) return;   // warp-uniform
+            const int np = nc >> 1, hp = np >> 1;
+            float xi, yi, dummy;
+            upk2(XI[0], xi, dummy);
+            upk2(YI[0], yi, dummy);
+            // the sum of column pairs [q0, q0 + len) (+ the odd column for half 1)
+            auto half_sum = [&](bool second, const float4* t0, int len, float& vx, float& vy) {
+                f32x2 AX[1] = {pk2(0.f, 0.f)}, AY[1] = {pk2(0.f, 0.f)};
+                tile_pairs2<1>(t0, len, 0, 1, XI, YI, AX, AY);
+                float a0, a1, b0, b1;
+                upk2(AX[0], a0, a1);
+                upk2(AY[0], b0, b1);
+                vx = a0 + a1;
+                vy = b0 + b1;
+                if (second && (nc & 1)) {
+                    const float2 pc = tile_col(tile, nc - 1);
+                    rep_pair(xi, yi, pc.x, pc.y, vx, vy);
+                }
+            };
+            float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
+            if (pfold) {   // half-warps on the two halves (the same length unless np is odd)
+                const bool second = lane >= 16;
+                f32x2 AX[1] = {pk2(0.f, 0.f)}, AY[1] = {pk2(0.f, 0.f)};
+                tile_pairs2<1>(tile + (second ? hp : 0), hp, 0, 1, XI, YI, AX, AY);
+                if (second && (np & 1)) tile_pairs2<1>(tile + 2 * hp, 1, 0, 1, XI, YI, AX, AY);
+                float a0, a1, b0, b1;
+                upk2(AX[0], a0, a1);
+                upk2(AY[0], b0, b1);
+                float vx = a0 + a1, vy = b0 + b1;
+                if (second && (nc & 1)) {
+                    const float2 pc = tile_col(tile, nc - 1);
+                    rep_pair(xi, yi, pc.x, pc.y, vx, vy);
+                }
+                if (second) {
+                    ax1 = vx;
+                    ay1 = vy;
                 } else {
-                    sx[m] += ax;
-                    sy[m] += ay;
+                    ax0 = vx;
+                    ay0 = vy;
+                }
+            } else {
+                if (hm & 1) half_sum(false, tile, hp, ax0, ay0);
+                if (hm & 2) half_sum(true, tile + hp, np - hp, ax1, ay1);
+            }
+            if (need[0]) {
+                if (hm & 1) {
+                    acc(sx[0][0], cx[0][0], ax0);
+                    acc(sy[0][0], cy[0][0], ay0);
+                }
+                if (hm & 2) {
+                    acc(sx[1][0], cx[1][0], ax1);
+                    acc(sy[1][0], cy[1][0], ay1);
+                }
+            }
+        } else {
+            int mlo, mhi;
+            need_range<RPT>(need, mlo, mhi);
+            if (mlo >= mhi) return;
+            f32x2 AX[RPT], AY[RPT];
+#pragma unroll
+            for (int m = 0; m < RPT; m++) AX[m] = AY[m] = pk2(0.f, 0.f);
+            tile_pairs2<RPT>(tile, nc >> 1, mlo, mhi, XI, YI, AX, AY);
+#pragma unroll
+            for (int m = 0; m < RPT; m++) {
+                float a0, a1, b0, b1, xi, yi, dummy;
+                upk2(AX[m], a0, a1);
+                upk2(AY[m], b0, b1);
+                upk2(XI[m], xi, dummy);
+                upk2(YI[m], yi, dummy);
+                float ax = a0 + a1, ay = b0 + b1;
+                if (nc & 1) {
+                    const float2 pc = tile_col(tile, nc - 1);
+                    rep_pair(xi, yi, pc.x, pc.y, ax, ay);
+                }
+                if (need[m]) {
+                    acc(sx[0][m], cx[0][m], ax);
+                    acc(sy[0][m], cy[0][m], ay);
                 }
             }
         }
@@ -322,14 +394,21 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         __syncthreads();
     }
 
-    // bulk: post the sums of the rows of batch kk into crep and restart them (the
-    // slot of a row among its batch's critical rows is fixed: cslot, set above)
+    // bulk: post the sums of the rows of batch kk into crep (half h at
+    // crep[h * CR + slot]; one sum per row: the second half is zero) and restart
+    // them (a row's slot among its batch's critical rows is fixed: cslot, set above)
     auto post_rows = [&](int kk, float2* crep) {
 #pragma unroll
         for (int m = 0; m < RPT; m++) {
             if (bi[m] == kk) {
-                crep[cslot[m]] = make_float2(sx[m] - cx[m], sy[m] - cy[m]);
-                sx[m] = sy[m] = cx[m] = cy[m] = 0.f;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    if (hm & (1 << h)) {
+                        crep[h * CR + cslot[m]] = make_float2(sx[h][m] - cx[h][m], sy[h][m] - cy[h][m]);
+                        sx[h][m] = sy[h][m] = cx[h][m] = cy[h][m] = 0.f;
+                    }
+                }
+                if (RPT > 1) crep[CR + cslot[m]] = make_float2(0.f, 0.f);
             }
         }
     };
@@ -548,7 +627,9 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 if (pre_ok || e1 - e0 > 32) {   // sums held by lane g
                     ax = hax_g; ay = hay_g; qx = hqx_g; qy = hqy_g;
                 }
-                float sxr = crep[c].x, cxr = 0.f, syr = crep[c].y, cyr = 0.f;
+                // the bulk sums' two column halves, first + second
+                float sxr = crep[c].x + crep[CR + c].x, cxr = 0.f;
+                float syr = crep[c].y + crep[CR + c].y, cyr = 0.f;
                 if (kprev >= 0) {
                     if (kahan) {
                         kahan_add(sxr, cxr, rxs);
@@ -695,7 +776,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             if (lane == 0) trace_mark(tk, rank, s, 3);
             bar_arrive_n(kBarTile, T);            // bulk may start step s
             const double e = ctl_critical(k, kprev, s % 3, s & 1, tile, (float)step, bnew, bold,
-                                          s_crep + (size_t)(s & 1) * CR, bnew, true);
+                                          s_crep + (size_t)(s & 1) * 2 * CR, bnew, true);
             if (lane == 0) trace_mark(tk, rank, s, 4);
             e_iter += e;
             __syncwarp();
@@ -748,7 +829,7 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 need[m] = bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
             if (tb == 0) trace_mark(tk, rank, s, 10);
             add_tile(tile, kpn, need);
-            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * CR);
+            post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * 2 * CR);
             if (tb == 0) trace_mark(tk, rank, s, 8);
             bar_arrive_n(kBarDone, T);
             // the staging warp: once the positions of step s+1 have landed, that step's
@@ -922,6 +1003,7 @@ static bl_status launch_grid_t(const ExactPlan& pl, const ExactTask& tk, const E
     if (pl.G > occ * device_sm_count())
         return set_error(BL_EINVAL, "exact engine: grid exceeds co-resident CTAs");
     ExactTask t = tk;
+    for (int w = 0; w < 16; w++) t.piece[w] = pl.piece[w];
     ExactParams p = prm;
     void* args[] = {&t, &p};
     BL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(pl.G), dim3(T), args, smem, st));
@@ -946,6 +1028,67 @@ static bl_status dispatch_rpt(const ExactPlan& pl, const ExactTask& tk, const Ex
     }
     return set_error(BL_EINVAL, "exact engine: unsupported rows per thread");
 }
+
+// Bulk pieces for one row per thread. The nloc rows of a CTA form blocks of 32;
+// a block is two units (its halves), and a last block of at most 16 rows is one
+// unit folded onto one warp. Each sub-partition gets an equal share of the units,
+// the control warp's the remainder, as whole blocks per warp plus at most one
+// single unit (a fold, or a half whose other half goes to another sub-partition). Bulk warp w runs on
+// sub-partition (w + 1) % 4. piece[w] = block | halves << 16 | fold << 18 (0: idle).
+// Returns false when the pieces do not fit the warps (the caller then gives each
+// warp one whole block in turn).
+static bool plan_pieces(int nloc, int NW, int* piece) {
+    const int nfull = nloc / 32, rem = nloc % 32;
+    const bool fold = rem > 0 && rem <= 16;
+    const int nwhole = nfull + (rem > 16 ? 1 : 0);   // blocks of two half units
+    const int U = 2 * nwhole + (fold ? 1 : 0);
+    std::vector<int> warps[4];
+    for (int w = 0; w < NW; w++) warps[(w + 1) % 4].push_back(w);
+    int budget[4] = {0, 0, 0, 0};
+    const int target = (U + 3) / 4;
+    int left = U;
+    for (int j = 1; j <= 3; j++) {
+        budget[j] = std::min({target, 2 * (int)warps[j].size(), left});
+        left -= budget[j];
+    }
+    budget[0] = std::min(left, 2 * (int)warps[0].size());
+    left -= budget[0];
+    for (int j = 1; j <= 3 && left > 0; j++) {   // what sub-partition 0 cannot hold
+        const int add = std::min(left, 2 * (int)warps[j].size() - budget[j]);
+        budget[j] += add;
+        left -= add;
+    }
+    if (left > 0) return false;
+    for (int w = 0; w < 16; w++) piece[w] = 0;
+    int next_block = 0, pending = -1;   // pending: second half of a split block
+    bool fold_left = fold;
+    for (int j : {1, 2, 3, 0}) {
+        int need = budget[j];
+        size_t wi = 0;
+        while (need >= 2 && next_block < nwhole && wi < warps[j].size()) {
+            piece[warps[j][wi++]] = next_block++ | (3 << 16);
+            need -= 2;
+        }
+        while (need > 0 && wi < warps[j].size()) {
+            if (fold_left) {
+                piece[warps[j][wi++]] = nfull | (1 << 18);
+                fold_left = false;
+            } else if (pending >= 0) {
+                piece[warps[j][wi++]] = pending | (2 << 16);
+                pending = -1;
+            } else if (next_block < nwhole) {
+                piece[warps[j][wi++]] = next_block | (1 << 16);
+                pending = next_block++;
+            } else {
+                return false;
+            }
+            need--;
+        }
+        if (need > 0) return false;
+    }
+    return next_block == nwhole && pending < 0 && !fold_left;
+}
+
 
 // Launch shape: G = one CTA per SM (at least 64 rows each); bulk threads TB and
 // rows per thread by the rows per CTA: up to 512 rows one row per thread, the
@@ -993,6 +1136,14 @@ bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* 
     out->G = G;
     out->T = T;
     out->rpt = chosen;
+    for (int w = 0; w < 16; w++) out->piece[w] = 0;
+    if (chosen == 1 && !plan_pieces(nloc, T / 32, out->piece)) {
+        const int NW = T / 32;   // one whole block per warp, the control warp's sub-partition last
+        for (int wb = 0; wb < NW; wb++) {
+            const int ws = (wb + 1) % 4 == 0 ? (NW - NW / 4) + (wb + 1) / 4 - 1 : wb - (wb + 1) / 4;
+            out->piece[wb] = 32 * ws < nloc ? (ws | (3 << 16)) : 0;
+        }
+    }
     out->crit_cap = div_up(std::min(BS, n), G) + 1;
     out->nbr_cap = 2048;
     while (EngineSmem(BS, nloc, out->crit_cap, out->nbr_cap, T / 32).total > 200 * 1024 &&

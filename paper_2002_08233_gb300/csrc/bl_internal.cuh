@@ -149,6 +149,7 @@ struct ExactTask {
     int nbr_cap;         // neighbour positions staged in shared memory
     unsigned long long* trace;   // optional phase timestamps [G][trace_steps][kTraceSlots]
     int trace_steps;
+    int piece[16];       // one row per thread: bulk warp w's rows (see exact_plan)
 };
 
 struct ExactParams {
@@ -166,6 +167,7 @@ struct ExactParams {
 struct ExactPlan {
     int G, T, rpt;
     int crit_cap, nbr_cap;   // see ExactTask
+    int piece[16];           // one row per thread: block | halves << 16 | fold << 18
 };
 bl_status exact_plan(int n, int BS, int ctas_hint, int threads_hint, ExactPlan* out);
 
