@@ -535,11 +535,32 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
             const int W = 1 << lw;
             const int g = lane >> lw, gl = lane & (W - 1);
             float rx = 0.f, ry = 0.f;
-            if (g < nr) {   // unrolled: the loads and reciprocals of 8 columns overlap
+            if (g < nr) {   // column pairs gl, gl + W, ... packed two columns an instruction
                 const float2 me = s_pos[lo + c0 + g];
-#pragma unroll 8
-                for (int q = gl; q < kpn; q += W) {
-                    const float2 pc = tile_col(tile, q);
+                const f32x2 X0 = pk2(me.x, me.x), Y0 = pk2(me.y, me.y), E = pk2(BL_EPS2, BL_EPS2);
+                f32x2 AX = pk2(0.f, 0.f), AY = pk2(0.f, 0.f);
+#pragma unroll 4
+                for (int q = gl; q < (kpn >> 1); q += W) {
+                    const float4 p = tile[q];
+                    const f32x2 X = pk2(p.x, p.y), Y = pk2(p.z, p.w);
+                    f32x2 dx, dy, d2;
+                    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(X0));
+                    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(Y0));
+                    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d2) : "l"(dy), "l"(E));
+                    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d2) : "l"(dx), "l"(d2));
+                    float da, db;
+                    upk2(d2, da, db);
+                    const f32x2 inv = pk2(rcp_sfu(da), rcp_sfu(db));
+                    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(AX) : "l"(dx), "l"(inv));
+                    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(AY) : "l"(dy), "l"(inv));
+                }
+                float a0, a1, b0, b1;
+                upk2(AX, a0, a1);
+                upk2(AY, b0, b1);
+                rx = a0 + a1;
+                ry = b0 + b1;
+                if ((kpn & 1) && gl == 0) {   // an odd last column: the group's first lane
+                    const float2 pc = tile_col(tile, kpn - 1);
                     rep_pair(me.x, me.y, pc.x, pc.y, rx, ry);
                 }
             }
