@@ -13,18 +13,23 @@
 // Launch shape: one persistent cooperative CTA per SM; row i belongs to CTA
 // (i mod G), so each minibatch's rows are spread over all CTAs (about BS/G
 // "critical" rows per CTA and batch). Inside a CTA the warps specialise:
-//   - 8 bulk warps keep their rows' positions and Kahan-compensated repulsion
-//     sums in registers and only run the pair loop: at step s = (t, k) they add
-//     the column tile of batch k-1 to every row that still needs it;
+//   - the bulk warps keep their rows' positions and repulsion sums (optionally
+//     Kahan-compensated) in registers and only run the pair loop: at step
+//     s = (t, k) they add the column tile of batch k-1 to every row that still
+//     needs it; with one row per thread, each row's sum is kept in two halves
+//     (the first and second half of every tile) so that the host can spread the
+//     work evenly over the SM's four sub-partitions (see plan_pieces);
 //   - one control warp runs the step chain: wait until all CTAs have published
 //     batch k-1 (monotonic counter, bounded spin), copy that column tile into
-//     shared memory, then for the CTA's rows of batch k add the tile, sum the
-//     CSR attraction and take back the neighbour repulsion, move each vertex by
+//     shared memory, then for the CTA's rows of batch k add the tile, add the CSR
+//     attraction and take back the neighbour repulsion, move each vertex by
 //     Step * ct/|ct| (Algorithm 2's update), publish and arrive on the counter;
-//   - the last bulk warp also stages the next rows' neighbour positions with
-//     cp.async (ids two steps ahead, positions one step ahead).
-// The roles meet at two named barriers per step (tile ready / bulk done), so the
-// latency of the step chain hides behind the bulk warps' pair work. The pair
+//   - the last bulk warp stages the next rows' neighbour positions with cp.async
+//     (ids two steps ahead, positions one step ahead) and, once they have landed,
+//     sums those rows' CSR terms over every neighbour but the ones in the batch
+//     moving now; the control warp adds just those from the next tile.
+// The roles meet at named barriers (tile ready / bulk done / CSR sums ready), so
+// the latency of the step chain hides behind the bulk warps' pair work. The pair
 // loop uses packed FP32x2 arithmetic (two columns per instruction) and one SFU
 // reciprocal per pair.
 //
