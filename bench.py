@@ -255,7 +255,7 @@ def run_exact(args, rank, world, local):
                      "frac": achieved / peak_pairs,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch
                      # (10 iterations) of this kernel on this workload
-                     "traffic": 2963968, "traffic_unit": "bytes per launch",
+                     "traffic": 3028992, "traffic_unit": "bytes per launch",
                      "kernel": "exact_grid_kernel",
                      "peak_source": f"{SMS} SMs x {MUFU_PER_CLK_PER_SM} SFU lanes/clk x "
                                     f"{sm_max:.0f} MHz ({src} sm_max_mhz)"},
@@ -450,7 +450,7 @@ def run_bh(args, local, steps=5, warmup=2):
                      "frac": achieved / hbm,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the 42
                      # kernels of one R-MAT scale-20 iteration (edge pass to energy)
-                     "traffic": 736400000 if args.bh_scale == 20 else None,
+                     "traffic": 736145152 if args.bh_scale == 20 else None,
                      "traffic_unit": "bytes per iteration",
                      "algorithmic_bytes_per_iteration": tbytes,
                      "bytes_note": "172 n + 12 nnz (+ 32 B per tree node over 2n): bbox, Morton, 4 sort "
