@@ -394,21 +394,41 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
             st_relaxed_u32(my, kFlagInc | tot);
         } else {
             st_relaxed_u32(my, kFlagAgg | tot);
+            // look back four predecessors at a time (their loads in flight together),
+            // adding their counts in order until an inclusive one
             unsigned long long t0 = 0;
             for (int pred = tile - 1; pred >= 0;) {
-                const unsigned v = ld_relaxed_u32(status + (size_t)pred * 256 + d);
-                if ((v & ~kCountMask) == 0u) {   // not published yet: bounded wait
-                    __nanosleep(32);
-                    if (t0 == 0) t0 = global_ns();
-                    else if (global_ns() - t0 > kWaitLimitNs) {
-                        atomicCAS(err, 0, (int)BL_ETIMEOUT);
-                        break;
+                unsigned v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    v[u] = pred - u >= 0 ? ld_relaxed_u32(status + (size_t)(pred - u) * 256 + d) : kFlagInc;
+                bool done = false, waiting = false;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (done || waiting) continue;
+                    if (pred - u < 0) {
+                        done = true;
+                        continue;
                     }
+                    if ((v[u] & ~kCountMask) == 0u) {   // not published yet: wait for it
+                        waiting = true;
+                        pred -= u;
+                        continue;
+                    }
+                    excl += v[u] & kCountMask;
+                    if (v[u] & kFlagInc) done = true;
+                }
+                if (done) break;
+                if (!waiting) {
+                    pred -= 4;
                     continue;
                 }
-                excl += v & kCountMask;
-                if (v & kFlagInc) break;
-                pred--;
+                __nanosleep(32);   // bounded wait for tile `pred`
+                if (t0 == 0) t0 = global_ns();
+                else if (global_ns() - t0 > kWaitLimitNs) {
+                    atomicCAS(err, 0, (int)BL_ETIMEOUT);
+                    break;
+                }
             }
             st_relaxed_u32(my, kFlagInc | (excl + tot));
         }
