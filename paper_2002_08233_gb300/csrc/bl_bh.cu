@@ -1131,22 +1131,23 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
 #pragma unroll
         for (int k = 0; k < 4; k++) g.j[k] = e + 32 * k < p.tk.z ? __ldg(&cols[e + 32 * k]) : -1;
     }
+    if (early) {
+        // one butterfly over lane l's own terms plus segment 1 + l's partial sum
+        if (slot != nullptr) {
+            const float2 w = unpack_pos(sv);
+            sx += w.x;
+            sy += w.y;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) finish_row(a, i, me, p.rp, p.od, sx, sy);
+        if (a.ttrace && lane == 0) a.ttrace[3 * (size_t)t + 2] = global_ns();
+        return true;
+    }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
     if (nseg <= 1) {
         if (lane == 0) finish_row(a, i, me, p.rp, p.od, sx, sy);
-    } else if (early) {
-        // the same fixed order as seg_wait: lane 0 starts from segment 0's sum, lane
-        // l adds segment 1 + l, then the butterfly
-        float tx = lane == 0 ? sx : 0.f, ty = lane == 0 ? sy : 0.f;
-        if (slot != nullptr) {
-            const float2 w = unpack_pos(sv);
-            tx += w.x;
-            ty += w.y;
-        }
-        tx = warp_sum(tx);
-        ty = warp_sum(ty);
-        if (lane == 0) finish_row(a, i, me, p.rp, p.od, tx, ty);
     } else if (seg > 0) {
         // a later segment: its partial sum goes to its slot for segment 0's warp
         if (lane == 0) publish_partial(&a.seg_sum[p.off + seg], sx, sy);
