@@ -1161,9 +1161,9 @@ __device__ __forceinline__ bool task_run_df(const SweepArgs& a, const TaskPre& p
     return true;
 }
 
-// two CTAs per SM (the launch's shape): the compiler may use 80 registers a thread
-// instead of squeezing to 64 (2.23 -> 2.18 ms per R-MAT 20 iteration)
-__global__ void __launch_bounds__(kSweepThreads, 2) dataflow_sweep_kernel(SweepArgs a) {
+// three CTAs per SM (the launch's shape): 80 registers a thread, no spills; more
+// warps for the tasks than two CTAs give (R-MAT 20 sweep 0.563 -> 0.552 ms)
+__global__ void __launch_bounds__(kSweepThreads, 3) dataflow_sweep_kernel(SweepArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -1500,7 +1500,7 @@ bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t call
     BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(iters, 1) * sizeof(double)));
     double step = 1.0;
     for (int64_t k = 0; k < L->t; k++) step *= 0.999;
-    int per_sm = 2;   // sweep CTAs per SM (measured best on R-MAT 20); BL_BH_SWEEP_CTAS overrides it
+    int per_sm = 3;   // sweep CTAs per SM (measured best on R-MAT 20); BL_BH_SWEEP_CTAS overrides it
     int occ = 0;
     BL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dataflow_sweep_kernel, kSweepThreads, 0));
     if (const char* e = std::getenv("BL_BH_SWEEP_CTAS")) per_sm = std::max(1, std::atoi(e));
