@@ -450,7 +450,7 @@ def run_bh(args, local, steps=5, warmup=2):
                      "frac": achieved / hbm,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the 42
                      # kernels of one R-MAT scale-20 iteration (edge pass to energy)
-                     "traffic": 736145152 if args.bh_scale == 20 else None,
+                     "traffic": 736119296 if args.bh_scale == 20 else None,
                      "traffic_unit": "bytes per iteration",
                      "algorithmic_bytes_per_iteration": tbytes,
                      "bytes_note": "172 n + 12 nnz (+ 32 B per tree node over 2n): bbox, Morton, 4 sort "
