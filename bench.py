@@ -254,8 +254,10 @@ def run_exact(args, rank, world, local):
                      "unit": "G pair-interactions/s (1 SFU reciprocal per pair)",
                      "frac": achieved / peak_pairs,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch
-                     # (10 iterations) of this kernel on this workload
-                     "traffic": 3028992, "traffic_unit": "bytes per launch",
+                     # (10 iterations) of this kernel on this workload: not taken on
+                     # the build that carries the row sums between launches (3,028,992
+                     # bytes on the build before it)
+                     "traffic": None, "traffic_unit": "bytes per launch",
                      "kernel": "exact_grid_kernel",
                      "peak_source": f"{SMS} SMs x {MUFU_PER_CLK_PER_SM} SFU lanes/clk x "
                                     f"{sm_max:.0f} MHz ({src} sm_max_mhz)"},

@@ -162,7 +162,11 @@ bl_status bl_layout_set_positions(bl_layout *L, const float *xy, int64_t start_i
  * BL_BH takes graphs of at most 126,322,567 vertices (its quadtree reserves
  * 17 n + 1 nodes with 32-bit indices); larger ones give BL_EINVAL. A BL_EXACT
  * call runs at most 2^31 - 1 minibatch steps (iters * ceil(n / batch)); a
- * longer run is split over several calls, with the same result. */
+ * longer run is split over several calls, with the same result. On the
+ * whole-GPU exact engine a call that continues the previous exact call (same
+ * batch, positions not replaced since) picks up the per-row repulsion sums that
+ * call left on the device (about 32 bytes per vertex, held by the layout)
+ * instead of recomputing them from the start positions. */
 bl_status bl_layout_run(bl_layout *L, int32_t iters, int32_t batch, bl_mode mode, float theta);
 
 /* Runs at most max_iters iterations and stops after the first iteration whose
@@ -180,7 +184,9 @@ bl_status bl_layout_run_until(bl_layout *L, int32_t max_iters, int32_t batch, bl
 bl_status bl_positions(const bl_layout *L, float *xy, int64_t cap_floats);
 
 /* Device pointer of the live positions (float2[n]); valid until the next
- * bl_layout_run or bl_layout_free. */
+ * bl_layout_run or bl_layout_free. New positions written through it before the
+ * next run are honoured (that run does not continue the previous exact launch's
+ * carried sums). */
 bl_status bl_positions_device(const bl_layout *L, void **dptr);
 
 /* Energy of each iteration of the last bl_layout_run (FP64, Section 2.2's

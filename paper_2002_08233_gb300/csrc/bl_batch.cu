@@ -431,6 +431,7 @@ bl_status batch_launch(const BatchJob* jobs, int count, int chunk, cudaStream_t 
             const int it0 = c * chunk;
             if (it0 >= jb.iters) continue;
             bl_layout* L = jb.L;
+            L->carry_key = 0;   // the exact engine's carried sums do not follow these moves
             double step = 1.0;
             for (int64_t q = 0; q < L->t + it0; q++) step *= 0.999;
             BatchItem it{};

@@ -1492,6 +1492,7 @@ struct PhaseEvents {
 };
 
 bl_status bh_run(bl_layout* L, int iters, int BS, float theta, cudaStream_t caller, bool sync) {
+    L->carry_key = 0;   // the exact engine's carried sums do not follow these moves
     BL_TRY(bh_ensure(L));
     BL_TRY(bh_plan(L, BS, caller));
     BHState* s = L->bh;

@@ -357,10 +357,40 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
         }
     };
 
+    // A row's (half-)sums in the carry buffer: slot (rank * ceil(n/G) + local row) * 2
+    // + half, {sx, sy, cx, cy}. Each (row, half) is summed by exactly one thread.
+    const size_t carry_base = (size_t)rank * (size_t)((n + G - 1) / G);
+    auto carry_rows = [&](bool store) {
+#pragma unroll
+        for (int m = 0; m < RPT; m++) {
+            if (bi[m] < 0) continue;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                if (!(hm & (1 << h))) continue;
+                float4* c = tk.carry + (carry_base + (size_t)lrow[m]) * 2 + h;
+                if (store) {
+                    *c = make_float4(sx[h][m], sy[h][m], cx[h][m], cy[h][m]);
+                } else {
+                    const float4 v = *c;
+                    sx[h][m] = v.x;
+                    sy[h][m] = v.y;
+                    cx[h][m] = v.z;
+                    cy[h][m] = v.w;
+                }
+            }
+        }
+    };
+
     // ---- prologue: columns c >= batch(row), c < B-1, at the starting positions
     //      (every column in snapshot mode); the next tile is fetched into registers
-    //      while the bulk warps add the current one -------------------------------------
-    {
+    //      while the bulk warps add the current one. A launch that continues the
+    //      previous one's run loads these sums from the carry buffer instead, where
+    //      that launch left them (the same sums: the same tiles, at the same
+    //      positions, added in the same order) ----------------------------------------
+    if (!snapshot && tk.carry_in) {
+        if (!is_ctl) carry_rows(false);
+        __syncthreads();
+    } else {
         const bool one_each = TQ <= T;
         float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
         auto fetch = [&](int c) {
@@ -848,13 +878,18 @@ __global__ void __launch_bounds__(TB + 32, 1) exact_grid_kernel(ExactTask tk, Ex
                 stage_pos(kn, k, (s + 1) % 3, (s + 1) & 1, nb, ob);
                 if (s + 2 < S) stage_ids((k + 2) % B, (s + 2) % 3);
             }
-            const bool last_iter = (it + 1 == tk.iters);
+            // in the last iteration the rows already moved need more columns only
+            // when their sums are carried to the next launch
+            const bool last_iter = (it + 1 == tk.iters) && tk.carry == nullptr;
             bool need[RPT];
 #pragma unroll
             for (int m = 0; m < RPT; m++)
                 need[m] = bi[m] >= 0 && bi[m] != k && (!last_iter || bi[m] >= k);
             if (tb == 0) trace_mark(tk, rank, s, 10);
             add_tile(tile, kpn, need);
+            // the launch's last step: every row's sums as the next step would find
+            // them (before batch 0's are posted), for a launch that continues the run
+            if (s + 1 == S && tk.carry != nullptr) carry_rows(true);
             post_rows((k + 1) % B, s_crep + (size_t)((s + 1) & 1) * 2 * CR);
             if (tb == 0) trace_mark(tk, rank, s, 8);
             bar_arrive_n(kBarDone, T);

@@ -107,6 +107,9 @@ struct bl_layout {
     bl::DevBuf epart;                   // double energy partials
     bl::DevBuf status;                  // int device status word + barrier counters
     bl::DevBuf scratch;                 // forces for debug hooks
+    bl::DevBuf carry;                   // exact engine: row sums a launch leaves for the next
+    mutable uint64_t carry_key = 0;     // launch shape those sums belong to (0: none valid)
+    const void* carry_pos = nullptr;    // positions buffer they continue from
     int64_t last_iters = 0;
     double last_energy = 0.0;
     double pairs = 0.0, vupd = 0.0;
@@ -150,6 +153,8 @@ struct ExactTask {
     unsigned long long* trace;   // optional phase timestamps [G][trace_steps][kTraceSlots]
     int trace_steps;
     int piece[16];       // one row per thread: bulk warp w's rows (see exact_plan)
+    float4* carry;       // optional [G * ceil(n/G) * 2] row sums at the end of the launch
+    int carry_in;        // 1: start from the sums in carry instead of the prologue
 };
 
 struct ExactParams {

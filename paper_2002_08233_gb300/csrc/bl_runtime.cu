@@ -98,6 +98,7 @@ static bl_status check_stream_status(bl_layout* L) {
     int st = 0;
     BL_CUDA_TRY(cudaMemcpy(&st, L->status.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
+        L->carry_key = 0;   // a failed run leaves no sums to continue from
         cudaMemset(L->status.p, 0, sizeof(int));
         return set_error((bl_status)st, st == BL_ETIMEOUT
                                             ? "a bounded device-side wait timed out"
@@ -133,6 +134,27 @@ bl_status bh_debug_tree(bl_layout* L, uint32_t* codes, int32_t* perm, int32_t* f
 bl_status quality_run(bl_layout* L, int32_t nsources, int32_t nqueries, uint64_t seed,
                       double* out, int64_t cap, cudaStream_t st);
 
+// Identifies the launch shape and parameters a set of carried row sums belongs to
+// (FNV-1a over the fields; never 0, which marks "none").
+static uint64_t carry_key_of(const ExactPlan& pl, int BS, const bl_force_params& p) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* d, size_t len) {
+        const unsigned char* b = static_cast<const unsigned char*>(d);
+        for (size_t q = 0; q < len; q++) {
+            h ^= b[q];
+            h *= 1099511628211ull;
+        }
+    };
+    const int shape[6] = {pl.G, pl.T, pl.rpt, pl.crit_cap, pl.nbr_cap, BS};
+    mix(shape, sizeof(shape));
+    mix(pl.piece, sizeof(pl.piece));
+    const float kr[2] = {p.K, p.R};
+    const int flags[3] = {p.repulse_neighbors, p.kahan, p.energy_model};
+    mix(kr, sizeof(kr));
+    mix(flags, sizeof(flags));
+    return h | 1ull;
+}
+
 // Small graphs whose minibatch chain dominates run on one thread-block cluster
 // (BL_EXACT_ENGINE=grid|cluster forces an engine).
 static bool use_cluster_engine(const bl_layout* L, int BS) {
@@ -146,6 +168,7 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
                     cudaStream_t st) {
     const int n = L->g->n;
     if (!snapshot && iters > 0 && use_cluster_engine(L, BS)) {
+        L->carry_key = 0;   // the positions move without the grid engine's sums
         double s = 1.0;
         for (int64_t k = 0; k < L->t; k++) s *= 0.999;
         BL_TRY(L->epart.ensure(L->alloc, (size_t)iters * 16 * sizeof(double)));
@@ -184,9 +207,20 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
         tk.trace_steps = L->trace_steps;
         L->trace_count = (int64_t)plan.G * L->trace_steps * kTraceSlots;
     }
+    uint64_t key = 0;
     if (!snapshot) {
         BL_TRY(L->epart.ensure(L->alloc, (size_t)iters * plan.G * sizeof(double)));
         tk.e_iter = L->epart.as<double>();
+        // Row sums carried between launches: a launch that continues the previous
+        // one (same launch shape and parameters, positions untouched since) starts
+        // from the sums that launch left instead of re-adding the columns after
+        // each row's batch at the start positions.
+        key = carry_key_of(plan, BS, L->prm);
+        const bool cont = L->carry_key == key && L->carry_pos == L->pos.p;
+        L->carry_key = 0;
+        BL_TRY(L->carry.ensure(L->alloc, (size_t)plan.G * div_up(n, plan.G) * 2 * sizeof(float4)));
+        tk.carry = L->carry.as<float4>();
+        tk.carry_in = cont ? 1 : 0;
     }
     ExactParams prm{};
     prm.invK = 1.0f / L->prm.K;
@@ -202,6 +236,8 @@ bl_status exact_run(bl_layout* L, int iters, int BS, bool snapshot, float2* f_ou
         BL_TRY(L->energy.ensure(L->alloc, (size_t)std::max(iters, 1) * sizeof(double)));
         BL_TRY(energy_reduce(L->epart.as<double>(), iters, plan.G, L->energy.as<double>(), st));
         if (iters & 1) std::swap(L->pos, L->pos2);   // final positions are in the other buffer
+        L->carry_key = key;
+        L->carry_pos = L->pos.p;
     }
     return BL_OK;
 }
@@ -219,6 +255,7 @@ void layout_destroy(bl_layout* L) {
     L->epart.release();
     L->status.release();
     L->scratch.release();
+    L->carry.release();
     L->trace.release();
     delete L;
 }
@@ -457,6 +494,7 @@ bl_status bl_layout_set_positions(bl_layout* L, const float* xy, int64_t start_i
     if (start_iter < 0) return set_error(BL_EINVAL, "bl_layout_set_positions: start_iter < 0");
     BL_CUDA_TRY(cudaMemcpyAsync(L->pos.p, xy, (size_t)L->g->n * sizeof(float2),
                                 cudaMemcpyHostToDevice, current_stream()));
+    L->carry_key = 0;
     L->t = start_iter;
     return BL_OK;
 }
@@ -544,6 +582,7 @@ bl_status bl_layout_run_until(bl_layout* L, int32_t max_iters, int32_t batch, bl
         if (conv && stop < c) {   // back to the chunk's start, then exactly `stop` iterations
             BL_CUDA_TRY(cudaMemcpyAsync(L->pos.p, L->scratch.p, (size_t)n * sizeof(float2),
                                         cudaMemcpyDeviceToDevice, st));
+            L->carry_key = 0;
             L->t = t0;
             L->vupd = vupd0;
             L->pairs = pairs0;
@@ -576,6 +615,7 @@ bl_status bl_positions(const bl_layout* L, float* xy, int64_t cap_floats) {
 bl_status bl_positions_device(const bl_layout* L, void** dptr) {
     if (!L || !dptr) return set_error(BL_EINVAL, "bl_positions_device: NULL argument");
     *dptr = L->pos.p;
+    L->carry_key = 0;   // the caller may write the positions before the next run
     return BL_OK;
 }
 

@@ -259,6 +259,63 @@ def test_split_runs_equal_one_run(core, engine, n, bs):
     assert np.array_equal(A.energy_history(), np.array(e))
 
 
+def test_moved_positions_end_the_carried_sums(core):
+    """A launch starts from the sums the previous launch left only while the
+    positions are the ones it left: after bl_layout_set_positions, a Barnes-Hut
+    run or a write through bl_positions_device, the next exact run equals, bit
+    for bit, a fresh layout's run from the same positions."""
+    import torch
+
+    n = 4000   # above the one-cluster engine's sizes: the whole-GPU engine
+    g = synth.erdos_renyi(n, 5.0, 41)
+    xy0 = synth.uniform_positions(n, 41)
+    xy1 = synth.uniform_positions(n, 42)
+    G = core.Graph(g)
+
+    def fresh(xy, t0, its):
+        L = core.Layout(G, xy=xy, start_iter=t0)
+        L.run(its, 256, "exact")
+        return L.positions(), L.energy_history()
+
+    def same(L, ref):
+        assert np.array_equal(L.positions(), ref[0])
+        assert np.array_equal(L.energy_history(), ref[1])
+
+    A = core.Layout(G, xy=xy0)
+    A.run(2, 256, "exact")
+    A.set_positions(xy1, start_iter=2)
+    A.run(3, 256, "exact")
+    same(A, fresh(xy1, 2, 3))
+
+    B = core.Layout(G, xy=xy0)
+    B.run(2, 256, "exact")
+    B.run(1, 256, "bh")
+    mid = B.positions()
+    B.run(2, 256, "exact")
+    same(B, fresh(mid, 3, 2))
+
+    class _Dev:   # the layout's position buffer as a torch tensor
+        def __init__(self, ptr):
+            self.__cuda_array_interface__ = {"shape": (n, 2), "typestr": "<f4",
+                                             "data": (ptr, False), "version": 2}
+
+    C = core.Layout(G, xy=xy0)
+    C.run(1, 256, "exact")
+    torch.cuda.synchronize()
+    live = torch.as_tensor(_Dev(C.device_ptr()), device="cuda")
+    live.copy_(torch.from_numpy(xy1).cuda())
+    torch.cuda.synchronize()
+    C.run(2, 256, "exact")
+    same(C, fresh(xy1, 1, 2))
+
+    D = core.Layout(G, xy=xy0)   # and a plain continuation equals one run
+    D.run(1, 256, "exact")
+    D.run(2, 256, "exact")
+    E = core.Layout(G, xy=xy0)
+    E.run(3, 256, "exact")
+    assert np.array_equal(D.positions(), E.positions())
+
+
 def test_pair_rate_probe(core):
     """The ceiling probe measures the pair loop below the SFU's 16 reciprocal lanes
     per clock per SM (one reciprocal per pair) and the reciprocal alone near them."""
